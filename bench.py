@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Throughput of SIMPLE Krylov-vector solves on a 100^3 cosine-stretched grid.
+
+One step = one Krylov-vector evaluation of Section 3 (Eqs. 8-10): the
+momentum predictor w = J.v of Eq. 10 followed by the SIMPLE-like projection
+loop (pressure-correction solve, velocity/pressure correction) until
+||phi_k||_inf <= 1e-8 ||phi_1||_inf.  Workload: lid parallel to the x
+sidewall, Re = 1900, 100^3 cosine-stretched grid, mixed precision (FP32
+sweeps inside the FP64 defect-correction loop); right-hand sides are 16
+seeded Gaussian velocity fields (seeds 1..16, 384 MB, more than the 126 MB
+L2) used in rotation.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(plain definition: J.v + exact tensor-product projection) on the same
+workload instead.  Under torchrun every rank runs its own replica (the path
+has no exchange step): value = all ranks' solves / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 100
+RE = 1900.0
+ALPHA = 0.0
+EPS = 1e-8
+NRHS = 16
+METRIC = "SIMPLE Krylov-vector solves/s (100^3, tol 1e-8)"
+WORKLOAD = "config 2 workload: 100^3 cosine grid, alpha=0, Re=1900, Krylov-vector solve to 1e-8"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[1]) for s in self.samples if len(s) >= 9 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) >= 9 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            if len(s) >= 9:
+                for nme, val in zip(names, s[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nme)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# algorithmic bytes per cell of one launch of each kernel class (FP64 state,
+# FP32 pressure-correction transforms)
+def algorithmic(kind, n, prec):
+    cells = n ** 3
+    f = 4 if prec == "mixed" else 8
+    if kind == "momentum":            # read U, v (3 x 8 B each), write w (3 x 8 B)
+        return {"bytes": 72 * cells}
+    if kind == "correct":             # read v, phi, p, write v, p, r
+        return {"bytes": (24 + f + 8 + 24 + 8 + 8) * cells}
+    if kind == "divergence":          # read v, write r
+        return {"bytes": 32 * cells}
+    if kind in ("tpf_x", "tpf_yz"):   # one 1-D transform: 2 n flop per cell
+        return {"flops": 2 * n * cells, "bytes": 2 * f * cells}
+    return {"bytes": 16 * cells}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import numpy as np
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1704_08521_gb300 as fv
+    import synth
+
+    n = args.n
+    shape = (n, n, n)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    g = fv.Grid(n, n, n, "cosine", alpha=ALPHA, re=RE)
+    U = torch.tensor(synth.vortex_base_flow(shape, "cosine", ALPHA), device=dev)
+    V = [torch.tensor(synth.gaussian_velocity(shape, 1 + s + 1000 * rank), device=dev) for s in range(NRHS)]
+    out = torch.empty(g.n_vel, dtype=torch.float64, device=dev)
+    p = torch.empty(g.n_cell, dtype=torch.float64, device=dev)
+
+    def step(s, prec=args.prec):
+        return fv.simple_krylov_solve(g, U, V[s % NRHS], out, p, eps=EPS, prec=prec)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for s in range(args.warmup):
+        st = step(s)
+    passes = []
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = fv.fv_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for s in range(args.steps):
+        passes.append(step(s)["passes"])
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    launches = fv.fv_launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * args.steps / (ms_max / 1e3)
+
+    # same workload in the plain FP64 form, a few steps (context for the
+    # mixed-precision speed-up; not the headline)
+    fp64 = None
+    if args.prec == "mixed":
+        k64 = max(3, min(args.steps, 10))
+        step(0, "fp64")
+        barrier()
+        e0.record(stream)
+        for s in range(k64):
+            step(s, "fp64")
+        e1.record(stream)
+        barrier()
+        fp64 = k64 / (e0.elapsed_time(e1) / 1e3)
+
+    # per-kernel-class device time over the same steps (profiled pass)
+    fv.fv_profile_enable(g, True)
+    for s in range(args.steps):
+        step(s)
+    prof = fv.fv_profile_read(g)
+    fv.fv_profile_enable(g, False)
+
+    # end to end through the public API: host (pinned) rhs in, result out
+    hin = [V[s].cpu().pin_memory() for s in range(min(NRHS, 4))]
+    hout = torch.empty(g.n_vel, dtype=torch.float64).pin_memory()
+    vin = torch.empty_like(out)
+    for s in range(2):
+        vin.copy_(hin[s % len(hin)], non_blocking=True)
+        fv.simple_krylov_solve(g, U, vin, out, p, eps=EPS, prec=args.prec)
+        hout.copy_(out, non_blocking=True)
+    barrier()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for s in range(args.steps):
+        vin.copy_(hin[s % len(hin)], non_blocking=True)
+        fv.simple_krylov_solve(g, U, vin, out, p, eps=EPS, prec=args.prec)
+        hout.copy_(out, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e = ws * args.steps / (float(t.item()) / 1e3)
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return None
+
+    # roofline of the dominant kernel class
+    pk = peaks()
+    kind = max(prof, key=lambda k: prof[k][0])
+    kms, kcount = prof[kind]
+    per_launch_s = kms / 1e3 / max(kcount, 1)
+    alg = algorithmic(kind, n, args.prec)
+    clock_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    if "flops" in alg:
+        # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x SM clock
+        peak = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12 if args.prec == "mixed" else None
+        achieved = alg["flops"] / per_launch_s / 1e12
+        roof = {"bound": "alu", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {clock_mhz:.0f} MHz (median under load)"}
+    else:
+        peak = pk.get("hbm_gbs", 6800.0)
+        achieved = alg["bytes"] / per_launch_s / 1e9
+        roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    step_ms = ms_max / args.steps
+    breakdown = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                     "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)}
+                 for k, v in prof.items() if v[1]}
+    # bytes moved per step
+    h2d = g.n_vel * 8
+    d2h = g.n_vel * 8
+    res = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 state / f32 sweeps" if args.prec == "mixed" else "f64",
+        "data": "synthetic (seeded Gaussian right-hand sides; analytic lid-driven-like base flow)",
+        "config": {"workload": WORKLOAD, "grid": f"{n}^3", "map": "cosine", "re": RE, "alpha": ALPHA,
+                   "tol": EPS, "prec": args.prec, "rhs_rotation": NRHS,
+                   "l2": f"inputs rotate over {NRHS} vectors ({NRHS * g.n_vel * 8 / 1e6:.0f} MB) > L2",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "simple_passes_mean": sum(passes) / len(passes),
+        "sweeps_per_s": value * sum(passes) / len(passes),
+        "mcell_jv_per_s": None,
+        "fp64_form_solves_per_s": fp64,
+        "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernel_breakdown": breakdown,
+        "clocks": clocks,
+    }
+    mom = prof.get("momentum")
+    if mom and mom[1]:
+        res["mcell_jv_per_s"] = n ** 3 / (mom[0] / 1e3 / mom[1]) / 1e6
+    if not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(n, budget_s=12.0)
+    if ws > 1:
+        dist.destroy_process_group()
+    return res
+
+
+def oracle_solver(n):
+    import numpy as np
+    import synth
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import layout
+    from oracle import grid as og, poisson, simple
+    shape = (n, n, n)
+    G = og.Grid(n, n, n, "cosine")
+    T = poisson.TPF(G)
+    U = layout.to_oracle(synth.vortex_base_flow(shape, "cosine", ALPHA), shape)
+    rhs = [layout.to_oracle(synth.gaussian_velocity(shape, 1 + s), shape) for s in range(2)]
+
+    def solve(s):
+        return simple.krylov_vector(G, T, U, rhs[s % 2], RE)
+    return solve
+
+
+def cores_used():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max(i.get("num_threads", 1) for i in info) if info else 1
+    except Exception:
+        return os.cpu_count()
+
+
+def cpu_baseline(n, budget_s=12.0):
+    solve = oracle_solver(n)
+    solve(0)
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < budget_s or k < 2:
+        solve(k)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "solves/s", "cores": cores_used(), "kind": "oracle",
+            "sample": f"{k} Krylov-vector solves of the {n}^3 workload (numpy FP64, exact projection)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    solve = oracle_solver(args.n)
+    for s in range(args.warmup):
+        solve(s)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        solve(s)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": f"{args.n}^3"},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores_used(), "kind": "oracle",
+                             "sample": f"{args.steps} Krylov-vector solves of the {args.n}^3 workload"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

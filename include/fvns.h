@@ -1,0 +1,218 @@
+/*
+ * fvns.h -- C ABI of the GB300 (sm_103a) library for the linear-stability
+ * method of A. Yu. Gelfgat, "Linear instability of the lid-driven flow in a
+ * cubic cavity" (arXiv 1704.08521).
+ *
+ * Problem (Section 2, Eqs. 1-4): incompressible flow in the unit cube,
+ * no-slip walls, the lid z = 1 moving with (u, v) = (cos alpha, sin alpha),
+ * Reynolds number Re.  Discretisation (Section 3): second-order staggered
+ * finite volumes on a stretched nx x ny x nz grid.
+ *
+ * ---------------------------------------------------------------- layout --
+ * Every array argument is a DEVICE pointer to float64 data owned by the
+ * caller (the library never frees it) unless a comment says "host".
+ *   cell field  : nz*ny*nx values, C order [k][j][i], i (x) fastest.
+ *   velocity    : 3 cell-sized blocks [u | v | w] (n_vel = 3*nz*ny*nx).
+ *                 u[k][j][i] is the x-velocity on the face x_i, the low face
+ *                 of cell i; u[k][j][0] is the wall x = 0.  Likewise
+ *                 v[k][0][i] and w[0][j][i] are walls.  Wall entries are
+ *                 ignored on input and written as 0 on output.  The high
+ *                 walls (x = 1, y = 1, z = 1) are not stored.
+ * The lid velocity of Eq. 4 is never stored: it enters through the stencils.
+ *
+ * ---------------------------------------------------------------- errors --
+ * Every call returns fv_status; on failure fv_last_error() gives a message
+ * (thread-local).  Invalid arguments give FV_EINVAL and launch nothing.
+ * Iteration caps give FV_ENOCONV with the stats filled in.  No call traps,
+ * asserts or exits.
+ *
+ * ---------------------------------------------------------------- streams --
+ * All work is queued on the stream given to fv_grid_create.  Calls that
+ * return host scalars (stats, eigenvalues) synchronise that stream.
+ */
+#ifndef FVNS_H
+#define FVNS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FV_OK = 0,
+  FV_EINVAL = 1,   /* bad size, null pointer, bad option */
+  FV_ENOMEM = 2,   /* device allocation failed */
+  FV_ECUDA = 3,    /* a CUDA call failed (message in fv_last_error) */
+  FV_ENOCONV = 4,  /* an iteration cap was reached */
+  FV_ENAN = 5,     /* a NaN/Inf appeared in a norm */
+  FV_ETIMEOUT = 6  /* reserved: a bounded device-side wait gave up */
+} fv_status;
+
+/* Grid stretching.  Section 3, Eq. 5: x -> x - 0.0975 sin(2 pi x) applied to
+ * the uniform points i/N (FV_MAP_SINE0975); FV_MAP_COSINE is
+ * x_i = (1 - cos(pi i / N)) / 2; FV_MAP_UNIFORM is x_i = i / N. */
+typedef enum { FV_MAP_SINE0975 = 0, FV_MAP_COSINE = 1, FV_MAP_UNIFORM = 2 } fv_map;
+
+/* Arithmetic of the stencil and pressure-correction sweeps.
+ * FV_FP64 : everything in float64.
+ * FV_MIXED: J.v and the tensor-product pressure-correction solve in float32
+ *           inside the float64 defect-correction loop of the SIMPLE-like
+ *           algorithm; divergence, correction and norms in float64. */
+typedef enum { FV_FP64 = 0, FV_MIXED = 1 } fv_prec;
+
+typedef struct fv_grid fv_grid; /* opaque: metrics, solver tables, workspace */
+
+typedef struct {
+  int nx, ny, nz;
+  int64_t n_cell; /* nx*ny*nz           */
+  int64_t n_vel;  /* 3*n_cell            */
+  int64_t n_unknown_vel; /* (nx-1)ny nz + nx(ny-1)nz + nx ny(nz-1) */
+  int64_t workspace_bytes; /* device memory the grid holds */
+} fv_grid_info;
+
+/* Options of one Krylov-vector evaluation (Section 3, the algorithm after
+ * Eq. 10).  Zero-initialised fields take the defaults in brackets. */
+typedef struct {
+  double eps;     /* stop when ||phi_k||_inf <= eps * ||phi_1||_inf  [1e-8] */
+  int max_pass;   /* cap on SIMPLE passes                            [200] */
+  int prec;       /* fv_prec                                 [FV_FP64 = 0] */
+  double omega;   /* under-relaxation of each correction, (0, 1]     [1.0] */
+  double sigma;   /* >0: return P(L_U v + sigma v) - sigma v, the shifted
+                     operator used inside GMRES and Arnoldi; 0: the plain
+                     Krylov vector P L_U v of Eqs. 8-9                 [0] */
+} fv_simple_opts;
+
+typedef struct {
+  int passes;          /* SIMPLE passes done                                */
+  double phi_first;    /* ||phi_1||_inf                                     */
+  double phi_last;     /* ||phi_last||_inf                                  */
+  double div_max;      /* max |D v_out| after the last pass                 */
+} fv_simple_stats;
+
+typedef struct {
+  double tol;        /* ||F||_inf target                              [1e-10] */
+  int max_newton;    /* Newton iteration cap                             [30] */
+  int gmres_m;       /* GMRES restart length (Section 3: 100)           [100] */
+  int gmres_max_it;  /* GMRES iteration cap per Newton step           [20000] */
+  double gmres_rtol; /* relative GMRES tolerance per Newton step       [1e-8] */
+  int prec;          /* fv_prec of the Krylov vectors           [FV_FP64 = 0] */
+  double sigma;      /* shift of the gradient complement                 [10] */
+  double simple_eps; /* SIMPLE tolerance inside GMRES                  [1e-10] */
+} fv_newton_opts;
+
+typedef struct {
+  int iterations;          /* Newton steps taken                        */
+  int gmres_total;         /* GMRES iterations summed over all steps    */
+  double res_hist[64];     /* ||F||_inf before each step (first 64)     */
+  double res_final;
+} fv_newton_stats;
+
+typedef struct {
+  double tol;        /* Ritz residual <= tol * max(|theta|, eps^(2/3))  [1e-10] */
+  int max_restarts;  /* implicit-restart cap                           [5000] */
+  int prec;          /* fv_prec of the Krylov vectors           [FV_FP64 = 0] */
+  double sigma;      /* shift of the gradient complement (must exceed minus
+                        the real part of every wanted eigenvalue)        [10] */
+  double simple_eps; /* SIMPLE tolerance per Krylov vector             [1e-10] */
+} fv_arnoldi_opts;
+
+typedef struct {
+  int restarts;
+  int matvecs;
+  double ritz_resid[64]; /* estimated residual of each returned pair */
+} fv_arnoldi_stats;
+
+/* Section 2-3: allocate a grid of nx x ny x nz finite volumes (each >= 4,
+ * <= 1024, n_vel < 2^31) with map fv_map, lid angle alpha (radians; 0 = lid
+ * parallel to the x sidewall, pi/4 = parallel to the diagonal plane) and
+ * Reynolds number re > 0.  `cuda_stream` is a cudaStream_t (NULL = legacy
+ * default stream).  Builds the metrics and the tensor-product eigenbases
+ * of the pressure-correction operator and allocates all workspace, so later
+ * calls never allocate.  *out receives the handle. */
+fv_status fv_grid_create(int nx, int ny, int nz, int map, double alpha, double re,
+                         void* cuda_stream, fv_grid** out);
+fv_status fv_grid_set_re(fv_grid* g, double re);
+fv_status fv_grid_set_stream(fv_grid* g, void* cuda_stream);
+fv_status fv_grid_get_info(const fv_grid* g, fv_grid_info* info /* host */);
+void fv_grid_destroy(fv_grid* g);
+const char* fv_last_error(void);
+
+/* Eqs. 1-4 discretised: steady residual of (U, P).
+ * F_mom[n_vel] = (1/Re) Lap U - div(U (x) U) - grad P at the velocity faces
+ * (lid velocity of Eq. 4 in the wall stencils), F_div[n_cell] = D U. */
+fv_status ns_residual(const fv_grid* g, const double* U, const double* P,
+                      double* F_mom, double* F_div);
+
+/* Eq. 6 / Eq. 10: Jv[n_vel] = (1/Re) Lap v - div(U (x) v) - div(v (x) U),
+ * the linearised momentum operator about U with homogeneous wall values
+ * (the momentum predictor w of Eq. 10).  prec selects float64 or float32
+ * arithmetic (inputs and output stay float64). */
+fv_status ns_jacvec(const fv_grid* g, const double* U, const double* v, double* Jv, int prec);
+
+/* Section 3, Eqs. 8-10 and the SIMPLE-like algorithm: from v_in compute
+ * w = L_U v_in (Eq. 10), then repeat { solve D G phi = D v (Neumann);
+ * v -= omega G phi; p += omega phi } until the stop test of opts.  Returns
+ * the divergence-free v_out[n_vel] and p_out[n_cell] (zero mean).
+ * v_in and v_out may not alias.  stats may be NULL. */
+fv_status simple_krylov_solve(const fv_grid* g, const double* U, const double* v_in,
+                              double* v_out, double* p_out,
+                              const fv_simple_opts* opts, fv_simple_stats* stats);
+
+/* Section 3, Newton steps 1-4 at the grid's current Re: U[n_vel] (in: guess,
+ * e.g. all zeros = rest; out: steady state) and P[n_cell] (out).  Each
+ * correction solves P L_U u = P F_mom by restarted GMRES(m) whose Krylov
+ * vectors come from simple_krylov_solve.  Returns FV_ENOCONV if
+ * ||F||_inf >= tol after max_newton steps. */
+fv_status newton_steady(fv_grid* g, double* U, double* P,
+                        const fv_newton_opts* opts, fv_newton_stats* stats);
+
+/* Section 3, Eq. 7: the nev (<= 64) eigenvalues of largest real part of the
+ * linearised operator about the steady U, by implicitly restarted Arnoldi
+ * (Krylov dimension m, nev + 2 <= m <= 128) in regular mode.  v0[n_vel] is
+ * the start vector (device; e.g. a seeded Gaussian; it is projected first).
+ * lam_re/lam_im (host, nev each) receive the eigenvalues sorted by
+ * descending real part, conjugate pairs adjacent (positive imaginary part
+ * first).  evec (device, optional, 2*n_vel: real then imaginary part)
+ * receives the leading eigenvector, unit W-norm, phase such that its
+ * largest-modulus entry is real positive. */
+fv_status arnoldi_leading(const fv_grid* g, const double* U, const double* v0,
+                          int m, int nev, double* lam_re, double* lam_im, double* evec,
+                          const fv_arnoldi_opts* opts, fv_arnoldi_stats* stats);
+
+/* W-weighted inner product <a, b> = sum over velocity faces of the momentum
+ * control-volume size times a b (wall faces excluded).  Result to host. */
+fv_status fv_dot_w(const fv_grid* g, const double* a, const double* b, double* out /* host */);
+
+/* Section 3 step 1 alone: phi[n_cell] = zero-mean solution of D G phi = r
+ * (Neumann) by the tensor-product factorisation; prec as above. */
+fv_status fv_pressure_solve(const fv_grid* g, const double* r, double* phi, int prec);
+
+/* ------------------------------------------------------- instrumentation --
+ * Kernel classes timed by the optional per-grid profiler (CUDA events
+ * recorded on the grid's stream around every launch of that class). */
+typedef enum {
+  FV_K_MOMENTUM = 0,   /* J.v / residual stencil                       */
+  FV_K_DIVERGENCE = 1, /* D v                                           */
+  FV_K_CORRECT = 2,    /* SIMPLE correction + divergence pass           */
+  FV_K_TPF_X = 3,      /* pressure solve: x-axis transforms             */
+  FV_K_TPF_YZ = 4,     /* pressure solve: y- and z-axis transforms      */
+  FV_K_DOTS = 5,       /* weighted inner products                       */
+  FV_K_VECTOR = 6,     /* other vector kernels (updates, scaling, ...)  */
+  FV_NKIND = 7
+} fv_kernel_kind;
+
+/* Start (on != 0) or stop recording; starting clears earlier records. */
+fv_status fv_profile_enable(fv_grid* g, int on);
+/* Synchronise the grid's stream and report, per fv_kernel_kind, the summed
+ * device time in ms and the number of launches since fv_profile_enable. */
+fv_status fv_profile_read(fv_grid* g, double* ms /* host, FV_NKIND */,
+                          int64_t* launches /* host, FV_NKIND */);
+/* Total number of kernels this library has launched in the process. */
+int64_t fv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FVNS_H */

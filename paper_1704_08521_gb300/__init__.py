@@ -1,0 +1,207 @@
+"""Python binding of libfvns (the C ABI in include/fvns.h).
+
+Argument marshalling only: every computation runs in the CUDA kernels of
+libfvns.so.  Device buffers are torch tensors (float64, CUDA, contiguous);
+their data pointers and the current torch stream are passed through.  There
+is no CPU fallback: importing this package fails loudly when the library is
+missing (build it with ``__graft_entry__.build()``).
+
+Storage layout (cell-indexed MAC, see include/fvns.h): a velocity vector of
+an nx x ny x nz grid holds 3 * nz * ny * nx values [u | v | w], each block
+C-ordered [k][j][i]; u[k][j][0], v[k][0][i], w[0][j][i] are walls (zero).
+"""
+import ctypes
+import math
+import os
+
+from ._lib import lib, FvError, check, STATUS_NAMES  # noqa: F401
+
+FV_MAP_SINE0975, FV_MAP_COSINE, FV_MAP_UNIFORM = 0, 1, 2
+MAPS = {"sine0975": FV_MAP_SINE0975, "cosine": FV_MAP_COSINE, "uniform": FV_MAP_UNIFORM}
+FV_FP64, FV_MIXED = 0, 1
+PRECS = {"fp64": FV_FP64, "mixed": FV_MIXED}
+
+
+class fv_grid_info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("n_cell", ctypes.c_int64), ("n_vel", ctypes.c_int64),
+                ("n_unknown_vel", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+
+class fv_simple_opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("max_pass", ctypes.c_int), ("prec", ctypes.c_int),
+                ("omega", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+
+class fv_simple_stats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int), ("phi_first", ctypes.c_double),
+                ("phi_last", ctypes.c_double), ("div_max", ctypes.c_double)]
+
+
+class fv_newton_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_newton", ctypes.c_int), ("gmres_m", ctypes.c_int),
+                ("gmres_max_it", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
+                ("prec", ctypes.c_int), ("sigma", ctypes.c_double),
+                ("simple_eps", ctypes.c_double)]
+
+
+class fv_newton_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("gmres_total", ctypes.c_int),
+                ("res_hist", ctypes.c_double * 64), ("res_final", ctypes.c_double)]
+
+
+class fv_arnoldi_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_restarts", ctypes.c_int), ("prec", ctypes.c_int),
+                ("sigma", ctypes.c_double), ("simple_eps", ctypes.c_double)]
+
+
+class fv_arnoldi_stats(ctypes.Structure):
+    _fields_ = [("restarts", ctypes.c_int), ("matvecs", ctypes.c_int),
+                ("ritz_resid", ctypes.c_double * 64)]
+
+
+def _ptr(t):
+    """Device pointer of a CUDA float64 contiguous tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f64(t, n, name):
+    import torch
+    if t.dtype != torch.float64 or t.numel() != n:
+        raise ValueError(f"{name}: expected {n} float64 values, got {t.numel()} {t.dtype}")
+    return _ptr(t)
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Grid:
+    """Owner of an fv_grid handle (Section 2-3: grid size, map, lid angle, Re)."""
+
+    def __init__(self, nx, ny, nz, map="cosine", alpha=0.0, re=1000.0, stream=None):
+        h = ctypes.c_void_p()
+        st = _stream() if stream is None else ctypes.c_void_p(stream)
+        check(lib.fv_grid_create(nx, ny, nz, MAPS[map] if isinstance(map, str) else int(map),
+                                 ctypes.c_double(alpha), ctypes.c_double(re), st,
+                                 ctypes.byref(h)), "fv_grid_create")
+        self.handle = h
+        self.shape = (nz, ny, nx)
+        self.n_cell = nx * ny * nz
+        self.n_vel = 3 * self.n_cell
+        self.alpha, self.re, self.map = alpha, re, map
+
+    def set_re(self, re):
+        check(lib.fv_grid_set_re(self.handle, ctypes.c_double(re)), "fv_grid_set_re")
+        self.re = re
+
+    def set_stream(self, stream):
+        check(lib.fv_grid_set_stream(self.handle, ctypes.c_void_p(stream)), "fv_grid_set_stream")
+
+    def info(self):
+        i = fv_grid_info()
+        check(lib.fv_grid_get_info(self.handle, ctypes.byref(i)), "fv_grid_get_info")
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.fv_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fv_grid_create(nx, ny, nz, map="cosine", alpha=0.0, re=1000.0, stream=None):
+    return Grid(nx, ny, nz, map, alpha, re, stream)
+
+
+def ns_residual(g, U, P, F_mom, F_div):
+    check(lib.ns_residual(g.handle, _f64(U, g.n_vel, "U"), _f64(P, g.n_cell, "P"),
+                          _f64(F_mom, g.n_vel, "F_mom"), _f64(F_div, g.n_cell, "F_div")),
+          "ns_residual")
+
+
+def ns_jacvec(g, U, v, Jv, prec="fp64"):
+    check(lib.ns_jacvec(g.handle, _f64(U, g.n_vel, "U"), _f64(v, g.n_vel, "v"),
+                        _f64(Jv, g.n_vel, "Jv"), PRECS.get(prec, prec)), "ns_jacvec")
+
+
+def simple_krylov_solve(g, U, v_in, v_out, p_out=None, eps=1e-8, max_pass=200, prec="fp64",
+                        omega=1.0, sigma=0.0):
+    o = fv_simple_opts(eps, max_pass, PRECS.get(prec, prec), omega, sigma)
+    s = fv_simple_stats()
+    check(lib.simple_krylov_solve(g.handle, _f64(U, g.n_vel, "U"), _f64(v_in, g.n_vel, "v_in"),
+                                  _f64(v_out, g.n_vel, "v_out"),
+                                  None if p_out is None else _f64(p_out, g.n_cell, "p_out"),
+                                  ctypes.byref(o), ctypes.byref(s)), "simple_krylov_solve")
+    return {"passes": s.passes, "phi_first": s.phi_first, "phi_last": s.phi_last,
+            "div_max": s.div_max}
+
+
+def newton_steady(g, U, P, tol=1e-10, max_newton=30, gmres_m=100, gmres_max_it=20000,
+                  gmres_rtol=1e-8, prec="fp64", sigma=10.0, simple_eps=1e-10, raise_on_fail=True):
+    o = fv_newton_opts(tol, max_newton, gmres_m, gmres_max_it, gmres_rtol, PRECS.get(prec, prec),
+                       sigma, simple_eps)
+    s = fv_newton_stats()
+    st = lib.newton_steady(g.handle, _f64(U, g.n_vel, "U"), _f64(P, g.n_cell, "P"),
+                           ctypes.byref(o), ctypes.byref(s))
+    out = {"status": st, "iterations": s.iterations, "gmres_total": s.gmres_total,
+           "res_hist": list(s.res_hist[:min(s.iterations + 1, 64)]), "res_final": s.res_final}
+    if raise_on_fail:
+        check(st, "newton_steady")
+    return out
+
+
+def arnoldi_leading(g, U, v0, m=30, nev=5, evec=None, tol=1e-10, max_restarts=5000,
+                    prec="fp64", sigma=10.0, simple_eps=1e-10):
+    lr = (ctypes.c_double * nev)()
+    li = (ctypes.c_double * nev)()
+    o = fv_arnoldi_opts(tol, max_restarts, PRECS.get(prec, prec), sigma, simple_eps)
+    s = fv_arnoldi_stats()
+    check(lib.arnoldi_leading(g.handle, _f64(U, g.n_vel, "U"), _f64(v0, g.n_vel, "v0"), m, nev,
+                              lr, li, None if evec is None else _f64(evec, 2 * g.n_vel, "evec"),
+                              ctypes.byref(o), ctypes.byref(s)), "arnoldi_leading")
+    lam = [complex(lr[i], li[i]) for i in range(nev)]
+    return lam, {"restarts": s.restarts, "matvecs": s.matvecs,
+                 "ritz_resid": list(s.ritz_resid[:nev])}
+
+
+def fv_dot_w(g, a, b):
+    out = ctypes.c_double()
+    check(lib.fv_dot_w(g.handle, _f64(a, g.n_vel, "a"), _f64(b, g.n_vel, "b"), ctypes.byref(out)),
+          "fv_dot_w")
+    return out.value
+
+
+def fv_pressure_solve(g, r, phi, prec="fp64"):
+    check(lib.fv_pressure_solve(g.handle, _f64(r, g.n_cell, "r"), _f64(phi, g.n_cell, "phi"),
+                                PRECS.get(prec, prec)), "fv_pressure_solve")
+
+
+KERNEL_KINDS = ["momentum", "divergence", "correct", "tpf_x", "tpf_yz", "dots", "vector"]
+
+
+def fv_profile_enable(g, on=True):
+    check(lib.fv_profile_enable(g.handle, 1 if on else 0), "fv_profile_enable")
+
+
+def fv_profile_read(g):
+    ms = (ctypes.c_double * len(KERNEL_KINDS))()
+    n = (ctypes.c_int64 * len(KERNEL_KINDS))()
+    check(lib.fv_profile_read(g.handle, ms, n), "fv_profile_read")
+    return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def fv_launch_count():
+    return int(lib.fv_launch_count())

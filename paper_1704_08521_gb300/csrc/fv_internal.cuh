@@ -1,0 +1,181 @@
+// Internal declarations of the fvns library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fvns.h"
+
+namespace fv {
+
+// ---------------------------------------------------------------- errors --
+void set_error(const std::string& msg);
+fv_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define FV_CUDA(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) return ::fv::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define FV_CHECK_LAUNCH() FV_CUDA(cudaGetLastError())
+
+#define FV_TRY(call)                      \
+  do {                                    \
+    fv_status s_ = (call);                \
+    if (s_ != FV_OK) return s_;           \
+  } while (0)
+
+// ------------------------------------------------------------ metrics ----
+// Device view of the 1-D grid metrics (Section 3, Eq. 5 and the finite-volume
+// reading): per axis d, for n_d cells,
+//   idx[d][m] = 1/dx_m          (m = 0..n-1)
+//   idc[d][f] = 1/dc_f          (f = 0..n, half cells at the walls)
+//   th[d][f]  = (dx_{f-1}/2)/dc_f   linear-interpolation weight from the
+//               centres f-1, f to the face f (f = 1..n-1; 0 at walls)
+//   dx[d][m], dc[d][f]          (volumes of the inner product)
+template <typename T>
+struct Met {
+  int n[3];
+  int64_t ncell;
+  const T* idx[3];
+  const T* idc[3];
+  const T* th[3];
+  const T* dx[3];
+  const T* dc[3];
+};
+
+// Tensor-product eigenbasis of the Neumann operator D G along one axis.
+struct AxisBasis {
+  int n = 0;
+  int null_index = 0;          // index of the zero eigenvalue
+  std::vector<double> lam;     // n
+  std::vector<double> E;       // n x n row-major: phi[m] = sum_a E[m][a] phihat[a]
+  std::vector<double> Einv;    // n x n row-major: rhat[a] = sum_m Einv[a][m] r[m]
+};
+
+template <typename T>
+struct TpfDev {
+  int n[3];
+  int null_index[3];
+  const T* E[3];
+  const T* Einv[3];
+  const T* lam[3];
+};
+
+}  // namespace fv
+
+struct fv_grid {
+  int n[3];
+  int64_t ncell, nvel;
+  int map;
+  double alpha, re;
+  cudaStream_t stream;
+
+  // host copies
+  std::vector<double> h_x[3], h_dx[3], h_dc[3];
+  fv::AxisBasis basis[3];
+
+  // device allocations
+  void* d_met_d = nullptr;   // double metrics (packed)
+  void* d_met_f = nullptr;   // float metrics
+  void* d_tpf_d = nullptr;   // double E/Einv/lam
+  void* d_tpf_f = nullptr;   // float E/Einv/lam
+  fv::Met<double> met_d;
+  fv::Met<float> met_f;
+  fv::TpfDev<double> tpf_d;
+  fv::TpfDev<float> tpf_f;
+
+  // workspace
+  double* vel_buf[3] = {nullptr, nullptr, nullptr};   // n_vel each
+  double* cell_buf[3] = {nullptr, nullptr, nullptr};  // n_cell each
+  void* tpf_buf[2] = {nullptr, nullptr};              // n_cell doubles each (float use half)
+  double* d_scal = nullptr;      // 64 device scalars
+  double* d_part = nullptr;      // reduction partials
+  int64_t part_len = 0;
+  double* h_scal = nullptr;      // pinned host mirror of d_scal
+  int64_t ws_bytes = 0;
+
+  // optional per-kernel-class event timing
+  mutable bool prof_on = false;
+  mutable std::vector<cudaEvent_t> ev_pool;
+  mutable std::vector<int> ev_kind;     // kind of each recorded (start, stop) pair
+  mutable size_t ev_used = 0;
+
+  // Krylov basis (allocated on first use)
+  double* kry = nullptr;
+  int kry_cols = 0;
+  double* kry_small = nullptr;   // device small-matrix area
+};
+
+namespace fv {
+
+// scalar slots in d_scal
+enum {
+  S_PHI_MAX = 0,   // max |phi| of the last SIMPLE pass (as uint64 bits)
+  S_DIV_MAX = 1,   // max |D v|
+  S_NAN = 2,       // nonzero when a NaN was seen
+  S_RED = 8        // start of general reduction results (56 slots)
+};
+constexpr int kScalars = 64;
+
+// ------------------------------------------------------- instrumentation -
+// Every launch goes through LaunchScope: it counts the launch and, when the
+// grid's profiler is on, brackets it with CUDA events on the grid's stream.
+void count_launch();
+struct LaunchScope {
+  const fv_grid* g;
+  int kind;
+  size_t idx;
+  LaunchScope(const fv_grid* g_, int kind_);
+  ~LaunchScope();
+};
+
+// ------------------------------------------------------------- kernels ---
+// all launches are on g->stream; they return FV_OK or FV_ECUDA
+fv_status launch_momentum_jac(const fv_grid* g, const double* U, const double* v, double* out,
+                              int prec, double shift);
+fv_status launch_residual(const fv_grid* g, const double* U, const double* P,
+                          double* Fm, double* Fdiv);
+fv_status launch_divergence(const fv_grid* g, const double* v, double* r, double* maxabs_slot);
+// vout = vin - omega G phi (faces), p += omega phi (p may be null),
+// r = D vout, max|phi| and max|r| into the scalar slots (reset by caller)
+fv_status launch_correct_div(const fv_grid* g, const double* vin, double* vout,
+                             const void* phi, bool phi_is_float, double* p, double* r,
+                             double omega);
+fv_status launch_zero_walls(const fv_grid* g, double* v);
+
+// tensor-product pressure solve: phi = (D G)^+ r ; phi is float or double
+fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec);
+
+// vector kernels (weighted inner products, Gram-Schmidt)
+fv_status vec_dots(const fv_grid* g, const double* V, int64_t ldv, int nvec, const double* w,
+                   double* d_out /* nvec, device */);
+fv_status vec_update(const fv_grid* g, double* w, const double* V, int64_t ldv, int nvec,
+                     const double* d_h, double sign);
+fv_status vec_axpby(const fv_grid* g, int64_t n, double a, const double* x, double b,
+                    const double* y, double* out);
+fv_status vec_scale_by_device(const fv_grid* g, int64_t n, const double* x, const double* d_s,
+                              int mode, double* out);
+fv_status vec_combine(const fv_grid* g, const double* V, int64_t ldv, int nin,
+                      const double* d_C /* nin x nout, row-major */, int nout, double* out,
+                      int64_t ldo);
+fv_status vec_maxabs(const fv_grid* g, int64_t n, const double* x, double* slot);
+fv_status widen_float(const fv_grid* g, const float* src, double* dst, int64_t n);
+
+// scalar helpers
+fv_status reset_scalars(const fv_grid* g);
+fv_status fetch_scalars(const fv_grid* g, double* host /* kScalars */);
+double bits_to_double(double slot);
+
+// small dense linear algebra (host), used by the GMRES / Arnoldi drivers
+// H is m x m row-major upper Hessenberg.
+bool hess_eigenvalues(int m, const double* H, double* wr, double* wi);
+void francis_double_step(int m, double* H, double* Q, double s, double t);
+void single_shift_step(int m, double* H, double* Q, double mu);
+// y (complex, m) with (H - theta I) y ~ 0, unit 2-norm
+void hess_eigvec(int m, const double* H, double tr, double ti, double* yr, double* yi);
+}  // namespace fv

@@ -1,0 +1,725 @@
+// Krylov machinery of Section 3: the SIMPLE-like evaluation of a Krylov
+// vector (Eqs. 8-10 and the three-step loop), restarted GMRES(m) inside the
+// Newton method, and implicitly restarted Arnoldi for the leading
+// eigenvalues of Eq. 7.  Vector work (weighted inner products, classical
+// Gram-Schmidt applied twice, combinations) runs in FP64 kernels; the m x m
+// Hessenberg matrix is handled in FP64 by the small dense routines.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fv_internal.cuh"
+
+namespace fv {
+
+namespace {
+
+constexpr int kDotBlocks = 1216;     // 8 x 152 SMs
+constexpr int kDotChunk = 2048;      // elements staged per block iteration
+constexpr int kMaxVec = 130;
+
+// Momentum control-volume size of velocity entry e (0 on wall faces).
+__device__ __forceinline__ double face_weight(const Met<double>& m, int64_t e) {
+  const int64_t nc = m.ncell;
+  const int c = (int)(e / nc);
+  const int64_t cell = e - c * nc;
+  const int i = (int)(cell % m.n[0]);
+  const int64_t t = cell / m.n[0];
+  const int j = (int)(t % m.n[1]);
+  const int k = (int)(t / m.n[1]);
+  const int pos = (c == 0) ? i : (c == 1 ? j : k);
+  if (pos == 0) return 0.0;
+  const double wx = (c == 0) ? m.dc[0][i] : m.dx[0][i];
+  const double wy = (c == 1) ? m.dc[1][j] : m.dx[1][j];
+  const double wz = (c == 2) ? m.dc[2][k] : m.dx[2][k];
+  return wx * wy * wz;
+}
+
+// partial[v][block] = sum over the block's elements of W w V_v
+__global__ void __launch_bounds__(256) k_dots(Met<double> m, const double* __restrict__ V,
+                                              int64_t ldv, int nvec,
+                                              const double* __restrict__ w, int64_t n,
+                                              double* __restrict__ partial) {
+  __shared__ double ww[kDotChunk];
+  __shared__ double wacc[8][kMaxVec];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = threadIdx.x; v < 8 * kMaxVec; v += blockDim.x) (&wacc[0][0])[v] = 0.0;
+  for (int64_t e0 = (int64_t)blockIdx.x * kDotChunk; e0 < n; e0 += (int64_t)gridDim.x * kDotChunk) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) {
+      const int64_t e = e0 + t;
+      ww[t] = (e < n) ? face_weight(m, e) * w[e] : 0.0;
+    }
+    __syncthreads();
+    for (int v = 0; v < nvec; ++v) {
+      const double* Vv = V + (int64_t)v * ldv;
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < kDotChunk / 256; ++t) {
+        const int64_t e = e0 + t * 256 + threadIdx.x;
+        if (e < n) s += ww[t * 256 + threadIdx.x] * __ldg(Vv + e);
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) wacc[warp][v] += s;
+    }
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += wacc[q][v];
+    partial[(int64_t)v * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk,
+                                  double* __restrict__ out) {
+  __shared__ double red[256];
+  const int v = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[(int64_t)v * nblk + b];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[v] = red[0];
+}
+
+// w += sign * sum_v h[v] V_v
+__global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const double* __restrict__ V,
+                                                int64_t ldv, int nvec, const double* __restrict__ h,
+                                                double sign, int64_t n) {
+  __shared__ double hs[kMaxVec];
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) hs[v] = sign * h[v];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[e];
+    for (int v = 0; v < nvec; ++v) s += hs[v] * __ldg(V + (int64_t)v * ldv + e);
+    w[e] = s;
+  }
+}
+
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b,
+                        const double* __restrict__ y, double* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = a * x[e] + (y ? b * y[e] : 0.0);
+}
+
+// mode 0: out = x / s ; mode 1: out = x * s
+__global__ void k_scale_dev(int64_t n, const double* __restrict__ x, const double* __restrict__ s,
+                            int mode, double* __restrict__ out) {
+  const double f = mode == 0 ? 1.0 / s[0] : s[0];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = x[e] * f;
+}
+
+// out_c = sum_i V_i C[i][c], c < nout; 32 elements per block staged in
+// shared memory so out may alias the first columns of V.
+__global__ void __launch_bounds__(256) k_combine(const double* V, int64_t ldv, int nin,
+                                                 const double* __restrict__ C, int nout,
+                                                 double* out, int64_t ldo, int64_t n) {
+  extern __shared__ double sv[];   // nin x 32
+  const int el = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + el;
+  for (int i = grp; i < nin; i += 8) sv[i * 32 + el] = (e < n) ? V[(int64_t)i * ldv + e] : 0.0;
+  __syncthreads();
+  if (e >= n) return;
+  for (int c = grp; c < nout; c += 8) {
+    double s = 0.0;
+    for (int i = 0; i < nin; ++i) s += sv[i * 32 + el] * __ldg(C + (int64_t)i * nout + c);
+    out[(int64_t)c * ldo + e] = s;
+  }
+}
+
+__global__ void k_maxabs(int64_t n, const double* __restrict__ x, double* slot, double* nanslot) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = fabs(x[e]);
+    if (!(v <= 1e300)) *nanslot = 1.0;
+    else a = fmax(a, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    a = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if (threadIdx.x == 0)
+      atomicMax((unsigned long long*)slot, (unsigned long long)__double_as_longlong(a));
+  }
+}
+
+__global__ void k_widen(const float* __restrict__ s, double* __restrict__ d, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = double(s[e]);
+}
+
+inline unsigned grid1d(int64_t n, int per_block = 256) {
+  int64_t b = (n + per_block - 1) / per_block;
+  return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 16);
+}
+
+}  // namespace
+
+fv_status vec_dots(const fv_grid* g, const double* V, int64_t ldv, int nvec, const double* w,
+                   double* d_out) {
+  if (nvec <= 0) return FV_OK;
+  if (nvec > kMaxVec) { set_error("vec_dots: too many vectors"); return FV_EINVAL; }
+  const int64_t n = g->nvel;
+  const int nblk = (int)std::min<int64_t>(kDotBlocks, (n + kDotChunk - 1) / kDotChunk);
+  {
+    LaunchScope ls_(g, FV_K_DOTS);
+    k_dots<<<nblk, 256, 0, g->stream>>>(g->met_d, V, ldv, nvec, w, n, g->d_part);
+  }
+  FV_CHECK_LAUNCH();
+  {
+    LaunchScope ls_(g, FV_K_DOTS);
+    k_reduce_partials<<<nvec, 256, 0, g->stream>>>(g->d_part, nblk, d_out);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status vec_update(const fv_grid* g, double* w, const double* V, int64_t ldv, int nvec,
+                     const double* d_h, double sign) {
+  if (nvec <= 0) return FV_OK;
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_update<<<grid1d(g->nvel), 256, 0, g->stream>>>(w, V, ldv, nvec, d_h, sign, g->nvel);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status vec_axpby(const fv_grid* g, int64_t n, double a, const double* x, double b,
+                    const double* y, double* out) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_axpby<<<grid1d(n), 256, 0, g->stream>>>(n, a, x, b, y, out);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status vec_scale_by_device(const fv_grid* g, int64_t n, const double* x, const double* d_s,
+                              int mode, double* out) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_scale_dev<<<grid1d(n), 256, 0, g->stream>>>(n, x, d_s, mode, out);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status vec_combine(const fv_grid* g, const double* V, int64_t ldv, int nin, const double* d_C,
+                      int nout, double* out, int64_t ldo) {
+  const int64_t n = g->nvel;
+  const size_t smem = (size_t)nin * 32 * sizeof(double);
+  if (smem > 200 * 1024) { set_error("vec_combine: too many inputs"); return FV_EINVAL; }
+  if (smem > 48 * 1024)
+    FV_CUDA(cudaFuncSetAttribute(k_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_combine<<<(unsigned)((n + 31) / 32), 256, smem, g->stream>>>(V, ldv, nin, d_C, nout, out, ldo, n);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status vec_maxabs(const fv_grid* g, int64_t n, const double* x, double* slot) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_maxabs<<<grid1d(n), 256, 0, g->stream>>>(n, x, slot, g->d_scal + S_NAN);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status widen_float(const fv_grid* g, const float* src, double* dst, int64_t n) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_widen<<<grid1d(n), 256, 0, g->stream>>>(src, dst, n);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status reset_scalars(const fv_grid* g) {
+  FV_CUDA(cudaMemsetAsync(g->d_scal, 0, kScalars * sizeof(double), g->stream));
+  return FV_OK;
+}
+
+fv_status fetch_scalars(const fv_grid* g, double* host) {
+  FV_CUDA(cudaMemcpyAsync(g->h_scal, g->d_scal, kScalars * sizeof(double), cudaMemcpyDeviceToHost,
+                          g->stream));
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  std::memcpy(host, g->h_scal, kScalars * sizeof(double));
+  return FV_OK;
+}
+
+double bits_to_double(double slot) { return slot; }
+
+// ------------------------------------------------------------------------
+// SIMPLE loop (Section 3): from w in `cur` (overwritten), iterate
+//   phi = (D G)^+ D v ; v -= omega G phi ; p += omega phi
+// until ||phi_k|| <= eps ||phi_1||.  The result ends in `out` (== cur or
+// another buffer of n_vel); `spare` is scratch of n_vel.
+struct SimpleResult {
+  int passes = 0;
+  double phi_first = 0.0, phi_last = 0.0, div_max = 0.0;
+};
+
+static fv_status simple_loop(const fv_grid* g, double* cur, double* spare, double* out, double* p,
+                             double eps, int max_pass, int prec, double omega, SimpleResult* res) {
+  double* r = g->cell_buf[0];
+  void* phi = (void*)g->cell_buf[1];
+  FV_TRY(reset_scalars(g));
+  FV_TRY(launch_divergence(g, cur, r, nullptr));
+  if (p) FV_CUDA(cudaMemsetAsync(p, 0, g->ncell * sizeof(double), g->stream));
+  double h[kScalars];
+  double phi1 = 0.0;
+  res->passes = 0;
+  fv_status st = FV_ENOCONV;
+  for (int pass = 1; pass <= max_pass; ++pass) {
+    FV_TRY(tpf_solve(g, r, phi, prec));
+    FV_TRY(reset_scalars(g));
+    FV_TRY(launch_correct_div(g, cur, spare, phi, prec == FV_MIXED, p, r, omega));
+    std::swap(cur, spare);
+    FV_TRY(fetch_scalars(g, h));
+    res->passes = pass;
+    const double ph = h[S_PHI_MAX];
+    res->div_max = h[S_DIV_MAX];
+    if (h[S_NAN] != 0.0) { set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN; }
+    if (pass == 1) phi1 = ph;
+    res->phi_first = phi1;
+    res->phi_last = ph;
+    if (ph == 0.0 || ph <= eps * phi1) { st = FV_OK; break; }
+  }
+  if (cur != out) FV_CUDA(cudaMemcpyAsync(out, cur, g->nvel * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  if (st != FV_OK) set_error("SIMPLE loop reached max_pass");
+  return st;
+}
+
+// A_sigma x = P (L_U x + sigma x) - sigma x  (sigma = 0: the Krylov vector).
+// out must not alias x.  Uses vel_buf[0] as scratch.
+static fv_status krylov_apply(const fv_grid* g, const double* U, const double* x, double* out,
+                              double* p, double sigma, int prec, double eps, int max_pass,
+                              double omega, SimpleResult* res) {
+  FV_TRY(launch_momentum_jac(g, U, x, out, prec, sigma));
+  fv_status s = simple_loop(g, out, g->vel_buf[0], out, p, eps, max_pass, prec, omega, res);
+  if (s != FV_OK) return s;
+  if (sigma != 0.0) FV_TRY(vec_axpby(g, g->nvel, 1.0, out, -sigma, x, out));
+  return FV_OK;
+}
+
+// Project x in place onto divergence-free fields (p: optional pressure out).
+static fv_status project_inplace(const fv_grid* g, double* x, double* p, int prec, double eps,
+                                 SimpleResult* res) {
+  return simple_loop(g, x, g->vel_buf[0], x, p, eps, 200, prec, 1.0, res);
+}
+
+static fv_status ensure_krylov(fv_grid* g, int cols) {
+  if (g->kry && g->kry_cols >= cols) return FV_OK;
+  if (g->kry) { cudaFree(g->kry); g->kry = nullptr; }
+  if (g->kry_small) { cudaFree(g->kry_small); g->kry_small = nullptr; }
+  cudaError_t e = cudaMalloc((void**)&g->kry, (size_t)cols * g->nvel * sizeof(double));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    set_error("Krylov basis allocation failed");
+    return FV_ENOMEM;
+  }
+  FV_CUDA(cudaMalloc((void**)&g->kry_small, (size_t)(kMaxVec + 2) * (kMaxVec + 2) * sizeof(double)));
+  g->kry_cols = cols;
+  return FV_OK;
+}
+
+// CGS2 of w against V[0..j] in the W-inner product; returns h (j+1) and
+// ||w||_W on the host.
+static fv_status cgs2(const fv_grid* g, const double* V, int j1, double* w, double* h_host,
+                      double* wnorm) {
+  double* dh1 = g->kry_small;
+  double* dh2 = g->kry_small + kMaxVec;
+  double* dnn = g->kry_small + 2 * kMaxVec;
+  FV_TRY(vec_dots(g, V, g->nvel, j1, w, dh1));
+  FV_TRY(vec_update(g, w, V, g->nvel, j1, dh1, -1.0));
+  FV_TRY(vec_dots(g, V, g->nvel, j1, w, dh2));
+  FV_TRY(vec_update(g, w, V, g->nvel, j1, dh2, -1.0));
+  FV_TRY(vec_dots(g, w, g->nvel, 1, w, dnn));
+  std::vector<double> tmp(2 * kMaxVec + 1);
+  FV_CUDA(cudaMemcpyAsync(tmp.data(), g->kry_small, (2 * kMaxVec + 1) * sizeof(double),
+                          cudaMemcpyDeviceToHost, g->stream));
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  for (int i = 0; i < j1; ++i) h_host[i] = tmp[i] + tmp[kMaxVec + i];
+  *wnorm = std::sqrt(std::max(tmp[2 * kMaxVec], 0.0));
+  return FV_OK;
+}
+
+static fv_status dot_host(const fv_grid* g, const double* a, const double* b, double* out) {
+  double* d = g->kry_small ? g->kry_small + 2 * kMaxVec + 4 : g->d_scal + S_RED;
+  FV_TRY(vec_dots(g, a, g->nvel, 1, b, d));
+  FV_CUDA(cudaMemcpyAsync(g->h_scal + S_RED, d, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  *out = g->h_scal[S_RED];
+  return FV_OK;
+}
+
+static fv_status maxabs_host(const fv_grid* g, int64_t n, const double* x, double* out, bool* nan) {
+  FV_TRY(reset_scalars(g));
+  FV_TRY(vec_maxabs(g, n, x, g->d_scal + S_RED + 1));
+  double h[kScalars];
+  FV_TRY(fetch_scalars(g, h));
+  *out = h[S_RED + 1];
+  if (nan) *nan = h[S_NAN] != 0.0;
+  return FV_OK;
+}
+
+}  // namespace fv
+
+using namespace fv;
+
+static fv_status check_grid(const fv_grid* g, const char* who) {
+  if (!g) { set_error(std::string(who) + ": grid is NULL"); return FV_EINVAL; }
+  return FV_OK;
+}
+
+extern "C" {
+
+fv_status ns_residual(const fv_grid* g, const double* U, const double* P, double* F_mom,
+                      double* F_div) {
+  FV_TRY(check_grid(g, "ns_residual"));
+  if (!U || !P || !F_mom || !F_div) { set_error("ns_residual: NULL pointer"); return FV_EINVAL; }
+  return launch_residual(g, U, P, F_mom, F_div);
+}
+
+fv_status ns_jacvec(const fv_grid* g, const double* U, const double* v, double* Jv, int prec) {
+  FV_TRY(check_grid(g, "ns_jacvec"));
+  if (!U || !v || !Jv) { set_error("ns_jacvec: NULL pointer"); return FV_EINVAL; }
+  if (prec != FV_FP64 && prec != FV_MIXED) { set_error("ns_jacvec: bad prec"); return FV_EINVAL; }
+  if (v == Jv || U == Jv) { set_error("ns_jacvec: output aliases an input"); return FV_EINVAL; }
+  return launch_momentum_jac(g, U, v, Jv, prec, 0.0);
+}
+
+fv_status fv_dot_w(const fv_grid* g, const double* a, const double* b, double* out) {
+  FV_TRY(check_grid(g, "fv_dot_w"));
+  if (!a || !b || !out) { set_error("fv_dot_w: NULL pointer"); return FV_EINVAL; }
+  return dot_host(g, a, b, out);
+}
+
+fv_status simple_krylov_solve(const fv_grid* g, const double* U, const double* v_in, double* v_out,
+                              double* p_out, const fv_simple_opts* opts, fv_simple_stats* stats) {
+  FV_TRY(check_grid(g, "simple_krylov_solve"));
+  if (!U || !v_in || !v_out) { set_error("simple_krylov_solve: NULL pointer"); return FV_EINVAL; }
+  if (v_in == v_out) { set_error("simple_krylov_solve: v_in and v_out alias"); return FV_EINVAL; }
+  fv_simple_opts o = {};
+  if (opts) o = *opts;
+  if (o.eps <= 0.0) o.eps = 1e-8;
+  if (o.max_pass <= 0) o.max_pass = 200;
+  if (o.omega <= 0.0) o.omega = 1.0;
+  if (o.omega > 1.0 || (o.prec != FV_FP64 && o.prec != FV_MIXED) || o.sigma < 0.0) {
+    set_error("simple_krylov_solve: bad option");
+    return FV_EINVAL;
+  }
+  SimpleResult r;
+  fv_status s = krylov_apply(g, U, v_in, v_out, p_out, o.sigma, o.prec, o.eps, o.max_pass, o.omega, &r);
+  if (stats) {
+    stats->passes = r.passes;
+    stats->phi_first = r.phi_first;
+    stats->phi_last = r.phi_last;
+    stats->div_max = r.div_max;
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------- Newton --
+fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* opts,
+                        fv_newton_stats* stats) {
+  FV_TRY(check_grid(g, "newton_steady"));
+  if (!U || !P) { set_error("newton_steady: NULL pointer"); return FV_EINVAL; }
+  fv_newton_opts o = {};
+  if (opts) o = *opts;
+  if (o.tol <= 0) o.tol = 1e-10;
+  if (o.max_newton <= 0) o.max_newton = 30;
+  if (o.gmres_m <= 0) o.gmres_m = 100;
+  if (o.gmres_max_it <= 0) o.gmres_max_it = 20000;
+  if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-8;
+  if (o.sigma <= 0) o.sigma = 10.0;
+  if (o.simple_eps <= 0) o.simple_eps = 1e-10;
+  if (o.gmres_m > kMaxVec - 2 || (o.prec != FV_FP64 && o.prec != FV_MIXED)) {
+    set_error("newton_steady: bad option (gmres_m <= 128, prec)");
+    return FV_EINVAL;
+  }
+  const int m = o.gmres_m;
+  FV_TRY(ensure_krylov(g, m + 1));
+  const int64_t nv = g->nvel;
+  double* V = g->kry;
+  double* Fm = g->vel_buf[1];
+  double* du = g->vel_buf[2];
+  fv_newton_stats st = {};
+  SimpleResult sr;
+  // W-norm floor that keeps the max-norm residual well below tol
+  double wmin = 1e300;
+  for (int d = 0; d < 3; ++d)
+    for (double x : g->h_dx[d]) wmin = std::min(wmin, x);
+  const double atol = 1e-3 * o.tol * std::sqrt(0.5 * wmin * wmin * wmin);
+
+  for (int it = 0; it <= o.max_newton; ++it) {
+    // continuity part of the Newton correction: project U
+    FV_TRY(launch_zero_walls(g, U));
+    FV_TRY(project_inplace(g, U, nullptr, FV_MIXED, 1e-13, &sr));
+    // momentum residual with P = 0, projected: F_m = N(U) - G P(U), and
+    // P(U) = (D G)^+ D N(U) accumulated by the projection
+    FV_CUDA(cudaMemsetAsync(P, 0, g->ncell * sizeof(double), g->stream));
+    FV_TRY(launch_residual(g, U, P, Fm, nullptr));
+    FV_TRY(project_inplace(g, Fm, P, FV_MIXED, 1e-13, &sr));
+    double fmax, dmax;
+    bool nan1 = false, nan2 = false;
+    FV_TRY(maxabs_host(g, nv, Fm, &fmax, &nan1));
+    FV_TRY(launch_divergence(g, U, g->cell_buf[2], nullptr));
+    FV_TRY(maxabs_host(g, g->ncell, g->cell_buf[2], &dmax, &nan2));
+    const double res = std::max(fmax, dmax);
+    if (it < 64) st.res_hist[it] = res;
+    st.res_final = res;
+    st.iterations = it;
+    if (nan1 || nan2 || !std::isfinite(res)) {
+      if (stats) *stats = st;
+      set_error("newton_steady: NaN in the residual");
+      return FV_ENAN;
+    }
+    if (res < o.tol) {
+      if (stats) *stats = st;
+      return FV_OK;
+    }
+    if (it == o.max_newton) break;
+
+    // GMRES(m) for A_sigma du = Fm, du = 0 initially
+    FV_CUDA(cudaMemsetAsync(du, 0, nv * sizeof(double), g->stream));
+    double bnorm;
+    FV_TRY(dot_host(g, Fm, Fm, &bnorm));
+    bnorm = std::sqrt(bnorm);
+    const double stop = std::max(o.gmres_rtol * bnorm, atol);
+    int its = 0;
+    bool first = true;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol(m + 2);
+    while (true) {
+      // r = b - A du
+      if (first) {
+        FV_CUDA(cudaMemcpyAsync(V, Fm, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+      } else {
+        FV_TRY(krylov_apply(g, U, du, V, nullptr, o.sigma, o.prec, o.simple_eps, 200, 1.0, &sr));
+        FV_TRY(vec_axpby(g, nv, -1.0, V, 1.0, Fm, V));
+      }
+      first = false;
+      double beta;
+      FV_TRY(dot_host(g, V, V, &beta));
+      beta = std::sqrt(beta);
+      if (beta <= stop || its >= o.gmres_max_it) break;
+      FV_TRY(vec_axpby(g, nv, 1.0 / beta, V, 0.0, nullptr, V));
+      std::fill(gv.begin(), gv.end(), 0.0);
+      gv[0] = beta;
+      int jdone = 0;
+      for (int j = 0; j < m; ++j) {
+        double* w = V + (int64_t)(j + 1) * nv;
+        FV_TRY(krylov_apply(g, U, V + (int64_t)j * nv, w, nullptr, o.sigma, o.prec, o.simple_eps,
+                            200, 1.0, &sr));
+        double hn;
+        FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn));
+        if (hn > 0) FV_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+        H[(size_t)(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+          H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+        }
+        const double a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+        const double den = std::hypot(a, b);
+        cs[j] = den == 0 ? 1.0 : a / den;
+        sn[j] = den == 0 ? 0.0 : b / den;
+        H[(size_t)j * m + j] = den;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        gv[j + 1] = -sn[j] * gv[j];
+        gv[j] = cs[j] * gv[j];
+        ++its;
+        jdone = j + 1;
+        if (std::fabs(gv[j + 1]) <= stop || its >= o.gmres_max_it || hn == 0) break;
+      }
+      // y = R^{-1} g ; du += V y
+      std::vector<double> y(jdone);
+      for (int i = jdone - 1; i >= 0; --i) {
+        double s = gv[i];
+        for (int k = i + 1; k < jdone; ++k) s -= H[(size_t)i * m + k] * y[k];
+        y[i] = s / H[(size_t)i * m + i];
+      }
+      FV_CUDA(cudaMemcpyAsync(g->kry_small, y.data(), jdone * sizeof(double), cudaMemcpyHostToDevice,
+                              g->stream));
+      FV_TRY(vec_update(g, du, V, nv, jdone, g->kry_small, 1.0));
+      FV_CUDA(cudaStreamSynchronize(g->stream));
+    }
+    st.gmres_total += its;
+    FV_TRY(vec_axpby(g, nv, 1.0, U, -1.0, du, U));
+  }
+  if (stats) *stats = st;
+  set_error("newton_steady: no convergence within max_newton");
+  return FV_ENOCONV;
+}
+
+// --------------------------------------------------------------- Arnoldi --
+fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, int m, int nev,
+                          double* lam_re, double* lam_im, double* evec,
+                          const fv_arnoldi_opts* opts, fv_arnoldi_stats* stats) {
+  fv_grid* g = const_cast<fv_grid*>(gc);
+  FV_TRY(check_grid(g, "arnoldi_leading"));
+  if (!U || !v0 || !lam_re || !lam_im) { set_error("arnoldi_leading: NULL pointer"); return FV_EINVAL; }
+  if (nev < 1 || nev > 64 || m < nev + 2 || m > 128) {
+    set_error("arnoldi_leading: need 1 <= nev <= 64 and nev + 2 <= m <= 128");
+    return FV_EINVAL;
+  }
+  fv_arnoldi_opts o = {};
+  if (opts) o = *opts;
+  if (o.tol <= 0) o.tol = 1e-10;
+  if (o.max_restarts <= 0) o.max_restarts = 5000;
+  if (o.sigma <= 0) o.sigma = 10.0;
+  if (o.simple_eps <= 0) o.simple_eps = 1e-10;
+  if (o.prec != FV_FP64 && o.prec != FV_MIXED) { set_error("arnoldi_leading: bad prec"); return FV_EINVAL; }
+  FV_TRY(ensure_krylov(g, m + 1));
+  const int64_t nv = g->nvel;
+  double* V = g->kry;
+  SimpleResult sr;
+  // v_0 = P x_0 / ||P x_0||
+  FV_CUDA(cudaMemcpyAsync(V, v0, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  FV_TRY(launch_zero_walls(g, V));
+  FV_TRY(project_inplace(g, V, nullptr, FV_MIXED, 1e-13, &sr));
+  double nrm;
+  FV_TRY(dot_host(g, V, V, &nrm));
+  if (!(nrm > 0)) { set_error("arnoldi_leading: start vector has no solenoidal part"); return FV_EINVAL; }
+  FV_TRY(vec_axpby(g, nv, 1.0 / std::sqrt(nrm), V, 0.0, nullptr, V));
+
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), hcol(m + 2);
+  std::vector<double> Hm((size_t)m * m), Q((size_t)m * m), wr(m), wi(m);
+  const int k_base = std::min(nev + (m - nev) / 2, m - 2);
+  int k = 0, matvecs = 0;
+  const double eps23 = std::pow(2.2204460492503131e-16, 2.0 / 3.0);
+  for (int restart = 0; restart < o.max_restarts; ++restart) {
+    for (int j = k; j < m; ++j) {
+      double* w = V + (int64_t)(j + 1) * nv;
+      FV_TRY(krylov_apply(g, U, V + (int64_t)j * nv, w, nullptr, o.sigma, o.prec, o.simple_eps,
+                          200, 1.0, &sr));
+      ++matvecs;
+      double hn;
+      FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn));
+      if (!(hn > 0) || !std::isfinite(hn)) { set_error("arnoldi_leading: breakdown"); return FV_ENAN; }
+      FV_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+      H[(size_t)(j + 1) * m + j] = hn;
+    }
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) Hm[(size_t)i * m + j] = H[(size_t)i * m + j];
+    if (!hess_eigenvalues(m, Hm.data(), wr.data(), wi.data())) {
+      set_error("arnoldi_leading: Hessenberg QR did not converge");
+      return FV_ENOCONV;
+    }
+    std::vector<int> ord(m);
+    for (int i = 0; i < m; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+      if (wr[a] != wr[b]) return wr[a] > wr[b];
+      return wi[a] > wi[b];
+    });
+    const double fnorm = std::fabs(H[(size_t)m * m + (m - 1)]);
+    std::vector<double> resid(nev), yr(m), yi(m);
+    int nconv = 0;
+    for (int q = 0; q < nev; ++q) {
+      const int id = ord[q];
+      hess_eigvec(m, Hm.data(), wr[id], wi[id], yr.data(), yi.data());
+      resid[q] = fnorm * std::hypot(yr[m - 1], yi[m - 1]);
+      const double sc = std::max(std::hypot(wr[id], wi[id]), eps23);
+      if (resid[q] <= o.tol * sc) ++nconv;
+    }
+    if (nconv >= nev) {
+      for (int q = 0; q < nev; ++q) { lam_re[q] = wr[ord[q]]; lam_im[q] = wi[ord[q]]; }
+      if (stats) {
+        stats->restarts = restart;
+        stats->matvecs = matvecs;
+        for (int q = 0; q < nev && q < 64; ++q) stats->ritz_resid[q] = resid[q];
+      }
+      if (evec) {
+        // leading Ritz vector x = V y (complex), unit W-norm, phase fixed
+        hess_eigvec(m, Hm.data(), wr[ord[0]], wi[ord[0]], yr.data(), yi.data());
+        std::vector<double> C((size_t)m * 2);
+        for (int i = 0; i < m; ++i) { C[2 * i] = yr[i]; C[2 * i + 1] = yi[i]; }
+        FV_CUDA(cudaMemcpyAsync(g->kry_small, C.data(), C.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, g->stream));
+        FV_TRY(vec_combine(g, V, nv, m, g->kry_small, 2, evec, nv));
+        double a2, b2;
+        FV_TRY(dot_host(g, evec, evec, &a2));
+        FV_TRY(dot_host(g, evec + nv, evec + nv, &b2));
+        const double inv = 1.0 / std::sqrt(a2 + b2);
+        // phase: largest-modulus entry real positive
+        std::vector<double> hx(2 * nv);
+        FV_CUDA(cudaMemcpyAsync(hx.data(), evec, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+        FV_CUDA(cudaStreamSynchronize(g->stream));
+        int64_t big = 0;
+        double bm = -1;
+        for (int64_t e = 0; e < nv; ++e) {
+          const double mm = hx[e] * hx[e] + hx[nv + e] * hx[nv + e];
+          if (mm > bm) { bm = mm; big = e; }
+        }
+        const double pr = hx[big] / std::sqrt(bm), pi = -hx[nv + big] / std::sqrt(bm);
+        // (a + i b)(pr + i pi) = (a pr - b pi) + i (a pi + b pr)
+        const double Cph[4] = {pr * inv, pi * inv, -pi * inv, pr * inv};
+        FV_CUDA(cudaMemcpyAsync(g->kry_small, Cph, 4 * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+        FV_TRY(vec_combine(g, evec, nv, 2, g->kry_small, 2, evec, nv));
+        FV_CUDA(cudaStreamSynchronize(g->stream));
+      }
+      return FV_OK;
+    }
+    // implicit restart with the m - k unwanted Ritz values as exact shifts
+    k = k_base;
+    {
+      const int a = ord[k - 1], b = ord[k];
+      if (wi[a] != 0.0 && wi[b] == -wi[a] && wr[b] == wr[a]) ++k;
+    }
+    for (int i = 0; i < m * m; ++i) Q[i] = 0.0;
+    for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
+    for (int q = k; q < m; ++q) {
+      const int id = ord[q];
+      if (wi[id] != 0.0 && q + 1 < m && wi[ord[q + 1]] == -wi[id] && wr[ord[q + 1]] == wr[id]) {
+        francis_double_step(m, Hm.data(), Q.data(), 2.0 * wr[id], wr[id] * wr[id] + wi[id] * wi[id]);
+        ++q;
+      } else {
+        single_shift_step(m, Hm.data(), Q.data(), wr[id]);
+      }
+    }
+    // f = V Q e_{k+1} Hs[k][k-1] + f_m Q[m-1][k-1]; new V_k = V Q[:, :k]
+    const double fscale = H[(size_t)m * m + (m - 1)] * Q[(size_t)(m - 1) * m + (k - 1)];
+    const double bsub = Hm[(size_t)k * m + (k - 1)];
+    std::vector<double> C((size_t)(m + 1) * (k + 1), 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int c = 0; c < k; ++c) C[(size_t)i * (k + 1) + c] = Q[(size_t)i * m + c];
+    for (int i = 0; i < m; ++i) C[(size_t)i * (k + 1) + k] = Q[(size_t)i * m + k] * bsub;
+    C[(size_t)m * (k + 1) + k] = fscale;
+    FV_CUDA(cudaMemcpyAsync(g->kry_small, C.data(), C.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, g->stream));
+    FV_TRY(vec_combine(g, V, nv, m + 1, g->kry_small, k + 1, V, nv));
+    // re-orthogonalise f against the kept vectors, normalise
+    double* f = V + (int64_t)k * nv;
+    double hn;
+    FV_TRY(cgs2(g, V, k, f, hcol.data(), &hn));
+    FV_TRY(vec_axpby(g, nv, 1.0 / hn, f, 0.0, nullptr, f));
+    std::fill(H.begin(), H.end(), 0.0);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) H[(size_t)i * m + j] = Hm[(size_t)i * m + j];
+    H[(size_t)k * m + (k - 1)] = hn;
+  }
+  set_error("arnoldi_leading: max_restarts reached");
+  return FV_ENOCONV;
+}
+
+}  // extern "C"

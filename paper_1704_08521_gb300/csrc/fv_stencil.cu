@@ -1,0 +1,361 @@
+// Staggered finite-volume stencils (Section 3): the linearised momentum
+// operator of Eq. 6 / Eq. 10 (J.v), the steady residual of Eqs. 1-4, the
+// divergence (Eq. 1) and the fused SIMPLE correction + divergence pass.
+//
+// One thread per cell (i, j, k), x fastest, so neighbouring threads read
+// neighbouring addresses of every field; the three outputs of a cell are the
+// momentum balances of its low x-, y- and z-faces.  The scheme:
+//   diffusion  : two-point gradients, half-cell distance to a wall value;
+//   convection : flux = (transport velocity) x (transported velocity), each
+//                linearly interpolated (distance weighted) to the control-
+//                volume face; wall fluxes vanish (zero normal velocity).
+#include "fv_internal.cuh"
+
+namespace fv {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T ld(const double* __restrict__ p, int64_t i) {
+  return T(__ldg(p + i));
+}
+
+// Momentum balance of component C at the face owned by cell (i, j, k).
+// JAC: (1/Re) Lap v - div(U (x) v) - div(v (x) U) + shift v   (homogeneous walls)
+// else: (1/Re) Lap U - div(U (x) U)                            (lid wall values)
+template <typename T, int C, bool JAC>
+__device__ __forceinline__ T momentum_face(const Met<T>& m, const double* __restrict__ U,
+                                           const double* __restrict__ V, int64_t base,
+                                           const int (&pos)[3], const int64_t (&st)[3],
+                                           T inv_re, T lid_hi, T shift) {
+  const int64_t nc = m.ncell;
+  const double* Uc = U + C * nc;
+  const double* Qc = (JAC ? V : U) + C * nc;
+  const int f = pos[C];
+  const int nC = m.n[C];
+
+  // ---- direction d = C (normal to the face): values on faces f-1, f, f+1
+  const T q0 = ld<T>(Qc, base);
+  const T qm = (f > 1) ? ld<T>(Qc, base - st[C]) : T(0);
+  const T qp = (f + 1 < nC) ? ld<T>(Qc, base + st[C]) : T(0);
+  T diff = ((qp - q0) * m.idx[C][f] - (q0 - qm) * m.idx[C][f - 1]) * m.idc[C][f];
+  T conv;
+  {
+    const T u0 = ld<T>(Uc, base);
+    const T um = (f > 1) ? ld<T>(Uc, base - st[C]) : T(0);
+    const T up = (f + 1 < nC) ? ld<T>(Uc, base + st[C]) : T(0);
+    T Fhi, Flo;
+    if (JAC) {
+      Fhi = T(0.5) * (u0 + up) * (q0 + qp);
+      Flo = T(0.5) * (um + u0) * (qm + q0);
+    } else {
+      Fhi = T(0.25) * (u0 + up) * (u0 + up);
+      Flo = T(0.25) * (um + u0) * (um + u0);
+    }
+    conv = (Fhi - Flo) * m.idc[C][f];
+  }
+
+  // ---- the two tangential directions
+#pragma unroll
+  for (int t = 1; t <= 2; ++t) {
+    const int d = (C + t) % 3;
+    const int e = pos[d];
+    const int nd = m.n[d];
+    // diffusion along d (cell centres e-1, e, e+1; walls at half cells)
+    const T wall_hi = (!JAC && d == 2) ? lid_hi : T(0);
+    const T sm = (e > 0) ? ld<T>(Qc, base - st[d]) : T(0);
+    const T sp = (e + 1 < nd) ? ld<T>(Qc, base + st[d]) : wall_hi;
+    diff += ((sp - q0) * m.idc[d][e + 1] - (q0 - sm) * m.idc[d][e]) * m.idx[d][e];
+
+    // convective fluxes through the d-faces e (low) and e+1 (high) of the
+    // C-control volume; the transport velocity a_d is interpolated along C
+    // from the centres f-1, f; the transported b_C along d from e-1, e.
+    const double* Ud = U + d * nc;
+    const double* Vd = V + d * nc;
+    const T thc = m.th[C][f];
+    T Flo = T(0), Fhi = T(0);
+    if (e > 0) {
+      const int64_t b = base;
+      const T aU = ld<T>(Ud, b - st[C]) + thc * (ld<T>(Ud, b) - ld<T>(Ud, b - st[C]));
+      const T thd = m.th[d][e];
+      const T cm = ld<T>(Uc, base - st[d]);
+      const T bU = cm + thd * (ld<T>(Uc, base) - cm);
+      if (JAC) {
+        const T aV = ld<T>(Vd, b - st[C]) + thc * (ld<T>(Vd, b) - ld<T>(Vd, b - st[C]));
+        const T bV = sm + thd * (q0 - sm);
+        Flo = aU * bV + aV * bU;
+      } else {
+        Flo = aU * bU;
+      }
+    }
+    if (e + 1 < nd) {
+      const int64_t b = base + st[d];
+      const T aU = ld<T>(Ud, b - st[C]) + thc * (ld<T>(Ud, b) - ld<T>(Ud, b - st[C]));
+      const T thd = m.th[d][e + 1];
+      const T c0 = ld<T>(Uc, base);
+      const T bU = c0 + thd * (ld<T>(Uc, base + st[d]) - c0);
+      if (JAC) {
+        const T aV = ld<T>(Vd, b - st[C]) + thc * (ld<T>(Vd, b) - ld<T>(Vd, b - st[C]));
+        const T bV = q0 + thd * (sp - q0);
+        Fhi = aU * bV + aV * bU;
+      } else {
+        Fhi = aU * bU;
+      }
+    }
+    conv += (Fhi - Flo) * m.idx[d][e];
+  }
+  T out = inv_re * diff - conv;
+  if (JAC) out += shift * q0;
+  return out;
+}
+
+template <typename T, bool JAC>
+__global__ void __launch_bounds__(256) k_momentum(Met<T> m, const double* __restrict__ U,
+                                                  const double* __restrict__ V,
+                                                  const double* __restrict__ P,
+                                                  double* __restrict__ out, T inv_re, T lid_u,
+                                                  T lid_v, T shift) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  const int k = blockIdx.z;
+  if (i >= m.n[0]) return;
+  const int pos[3] = {i, j, k};
+  const int64_t st[3] = {1, (int64_t)m.n[0], (int64_t)m.n[0] * m.n[1]};
+  const int64_t base = ((int64_t)k * m.n[1] + j) * m.n[0] + i;
+  const int64_t nc = m.ncell;
+  // u (x-faces)
+  {
+    T r = T(0);
+    if (i > 0) {
+      r = momentum_face<T, 0, JAC>(m, U, V, base, pos, st, inv_re, lid_u, shift);
+      if (!JAC) r -= T(__ldg(P + base) - __ldg(P + base - 1)) * m.idc[0][i];
+    }
+    out[base] = double(r);
+  }
+  // v (y-faces)
+  {
+    T r = T(0);
+    if (j > 0) {
+      r = momentum_face<T, 1, JAC>(m, U, V, base, pos, st, inv_re, lid_v, shift);
+      if (!JAC) r -= T(__ldg(P + base) - __ldg(P + base - st[1])) * m.idc[1][j];
+    }
+    out[nc + base] = double(r);
+  }
+  // w (z-faces)
+  {
+    T r = T(0);
+    if (k > 0) {
+      r = momentum_face<T, 2, JAC>(m, U, V, base, pos, st, inv_re, T(0), shift);
+      if (!JAC) r -= T(__ldg(P + base) - __ldg(P + base - st[2])) * m.idc[2][k];
+    }
+    out[2 * nc + base] = double(r);
+  }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* slot, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax((unsigned long long*)slot, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = (lane < nw) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+// D v (Eq. 1) at every cell; wall faces are read as zero.
+__global__ void __launch_bounds__(256) k_divergence(Met<double> m, const double* __restrict__ v,
+                                                    double* __restrict__ r, double* maxslot,
+                                                    double* nanslot) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  double a = 0.0;
+  if (i < m.n[0]) {
+    const int64_t nx = m.n[0], nxy = nx * m.n[1], nc = m.ncell;
+    const int64_t base = ((int64_t)k * m.n[1] + j) * nx + i;
+    const double u0 = (i > 0) ? v[base] : 0.0;
+    const double u1 = (i + 1 < m.n[0]) ? v[base + 1] : 0.0;
+    const double v0 = (j > 0) ? v[nc + base] : 0.0;
+    const double v1 = (j + 1 < m.n[1]) ? v[nc + base + nx] : 0.0;
+    const double w0 = (k > 0) ? v[2 * nc + base] : 0.0;
+    const double w1 = (k + 1 < m.n[2]) ? v[2 * nc + base + nxy] : 0.0;
+    const double div = (u1 - u0) * m.idx[0][i] + (v1 - v0) * m.idx[1][j] + (w1 - w0) * m.idx[2][k];
+    r[base] = div;
+    a = fabs(div);
+    if (!(a <= 1e300)) { *nanslot = 1.0; a = 0.0; }
+  }
+  if (maxslot) {
+    a = block_max(a);
+    if (threadIdx.x == 0) atomic_max_nonneg(maxslot, a);
+  }
+}
+
+// One SIMPLE pass after the pressure-correction solve (Section 3, step 2):
+// vout = vin - omega G phi on the faces owned by the cell, p += omega phi,
+// and the new divergence r = D vout, computed from the corrected high faces
+// on the fly (vin and vout are different buffers, so no thread reads a face
+// another thread has already overwritten).
+template <typename PT>
+__global__ void __launch_bounds__(256) k_correct_div(Met<double> m, const double* __restrict__ vin,
+                                                     double* __restrict__ vout,
+                                                     const PT* __restrict__ phi,
+                                                     double* __restrict__ p,
+                                                     double* __restrict__ r, double omega,
+                                                     double* scal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  double aphi = 0.0, adiv = 0.0;
+  if (i < m.n[0]) {
+    const int nx = m.n[0], ny = m.n[1], nz = m.n[2];
+    const int64_t sy = nx, sz = (int64_t)nx * ny, nc = m.ncell;
+    const int64_t base = ((int64_t)k * ny + j) * nx + i;
+    const double f0 = double(phi[base]);
+    // own (low) faces
+    double u0 = 0.0, v0 = 0.0, w0 = 0.0;
+    if (i > 0) u0 = vin[base] - omega * (f0 - double(phi[base - 1])) * m.idc[0][i];
+    if (j > 0) v0 = vin[nc + base] - omega * (f0 - double(phi[base - sy])) * m.idc[1][j];
+    if (k > 0) w0 = vin[2 * nc + base] - omega * (f0 - double(phi[base - sz])) * m.idc[2][k];
+    vout[base] = u0;
+    vout[nc + base] = v0;
+    vout[2 * nc + base] = w0;
+    // high faces, corrected on the fly
+    double u1 = 0.0, v1 = 0.0, w1 = 0.0;
+    if (i + 1 < nx) u1 = vin[base + 1] - omega * (double(phi[base + 1]) - f0) * m.idc[0][i + 1];
+    if (j + 1 < ny) v1 = vin[nc + base + sy] - omega * (double(phi[base + sy]) - f0) * m.idc[1][j + 1];
+    if (k + 1 < nz) w1 = vin[2 * nc + base + sz] - omega * (double(phi[base + sz]) - f0) * m.idc[2][k + 1];
+    const double div = (u1 - u0) * m.idx[0][i] + (v1 - v0) * m.idx[1][j] + (w1 - w0) * m.idx[2][k];
+    r[base] = div;
+    if (p) p[base] += omega * f0;
+    aphi = fabs(f0);
+    adiv = fabs(div);
+    if (!(aphi <= 1e300) || !(adiv <= 1e300)) {
+      scal[S_NAN] = 1.0;
+      aphi = adiv = 0.0;
+    }
+  }
+  aphi = block_max(aphi);
+  __syncthreads();
+  adiv = block_max(adiv);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(scal + S_PHI_MAX, aphi);
+    atomic_max_nonneg(scal + S_DIV_MAX, adiv);
+  }
+}
+
+__global__ void k_zero_walls(int nx, int ny, int nz, double* v) {
+  const int64_t nc = (int64_t)nx * ny * nz;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // u at i = 0: ny*nz entries; v at j = 0: nx*nz; w at k = 0: nx*ny
+  const int64_t a = (int64_t)ny * nz, b = (int64_t)nx * nz, c = (int64_t)nx * ny;
+  if (t < a) {
+    const int64_t kk = t / ny, jj = t % ny;
+    v[(kk * ny + jj) * nx] = 0.0;
+  } else if (t < a + b) {
+    const int64_t s = t - a, kk = s / nx, ii = s % nx;
+    v[nc + kk * ny * (int64_t)nx + ii] = 0.0;
+  } else if (t < a + b + c) {
+    const int64_t s = t - a - b;
+    v[2 * nc + s] = 0.0;
+  }
+}
+
+inline dim3 cell_grid(const fv_grid* g, int bx) {
+  return dim3((g->n[0] + bx - 1) / bx, g->n[1], g->n[2]);
+}
+
+inline int block_x(const fv_grid* g) {
+  return g->n[0] >= 128 ? 128 : (g->n[0] >= 64 ? 64 : 32);
+}
+
+}  // namespace
+
+fv_status launch_momentum_jac(const fv_grid* g, const double* U, const double* v, double* out,
+                              int prec, double shift) {
+  const int bx = block_x(g);
+  if (prec == FV_MIXED) {
+    {
+      LaunchScope ls_(g, FV_K_MOMENTUM);
+      k_momentum<float, true><<<cell_grid(g, bx), bx, 0, g->stream>>>(
+          g->met_f, U, v, nullptr, out, float(1.0 / g->re), 0.f, 0.f, float(shift));
+    }
+  } else {
+    {
+      LaunchScope ls_(g, FV_K_MOMENTUM);
+      k_momentum<double, true><<<cell_grid(g, bx), bx, 0, g->stream>>>(
+          g->met_d, U, v, nullptr, out, 1.0 / g->re, 0.0, 0.0, shift);
+    }
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_residual(const fv_grid* g, const double* U, const double* P, double* Fm,
+                          double* Fdiv) {
+  const int bx = block_x(g);
+  {
+    LaunchScope ls_(g, FV_K_MOMENTUM);
+    k_momentum<double, false><<<cell_grid(g, bx), bx, 0, g->stream>>>(
+        g->met_d, U, U, P, Fm, 1.0 / g->re, std::cos(g->alpha), std::sin(g->alpha), 0.0);
+  }
+  FV_CHECK_LAUNCH();
+  if (Fdiv) {
+    {
+      LaunchScope ls_(g, FV_K_DIVERGENCE);
+      k_divergence<<<cell_grid(g, bx), bx, 0, g->stream>>>(g->met_d, U, Fdiv, nullptr,
+                                                           g->d_scal + S_NAN);
+    }
+    FV_CHECK_LAUNCH();
+  }
+  return FV_OK;
+}
+
+fv_status launch_divergence(const fv_grid* g, const double* v, double* r, double* maxabs_slot) {
+  const int bx = block_x(g);
+  {
+    LaunchScope ls_(g, FV_K_DIVERGENCE);
+    k_divergence<<<cell_grid(g, bx), bx, 0, g->stream>>>(g->met_d, v, r, maxabs_slot,
+                                                         g->d_scal + S_NAN);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_correct_div(const fv_grid* g, const double* vin, double* vout, const void* phi,
+                             bool phi_is_float, double* p, double* r, double omega) {
+  const int bx = block_x(g);
+  if (phi_is_float)
+    {
+      LaunchScope ls_(g, FV_K_CORRECT);
+      k_correct_div<float><<<cell_grid(g, bx), bx, 0, g->stream>>>(
+          g->met_d, vin, vout, (const float*)phi, p, r, omega, g->d_scal);
+    }
+  else
+    {
+      LaunchScope ls_(g, FV_K_CORRECT);
+      k_correct_div<double><<<cell_grid(g, bx), bx, 0, g->stream>>>(
+          g->met_d, vin, vout, (const double*)phi, p, r, omega, g->d_scal);
+    }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_zero_walls(const fv_grid* g, double* v) {
+  const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  const int64_t tot = ny * nz + nx * nz + nx * ny;
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_zero_walls<<<(unsigned)((tot + 255) / 256), 256, 0, g->stream>>>(g->n[0], g->n[1], g->n[2], v);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+}  // namespace fv

@@ -1,0 +1,40 @@
+/*
+ * fvns_host.h -- host-only helpers of libfvns, exported so that the host
+ * logic of the library can be checked without a GPU.  None of them launches
+ * a kernel.
+ */
+#ifndef FVNS_HOST_H
+#define FVNS_HOST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Eigenvalues (wr + i wi, unordered) of the m x m row-major upper
+ * Hessenberg H by the Francis double-shift QR iteration, the dense step of
+ * the Arnoldi method of Section 3.  Returns 0, or 4 if it did not converge. */
+int fv_host_hess_eigenvalues(int m, const double* H, double* wr, double* wi);
+
+/* Apply nshift implicit shifted-QR steps to the Hessenberg H (in place) and
+ * accumulate them into Q (m x m, row-major): a conjugate pair (sr, +-si)
+ * as one Francis double-shift step, a real shift as a Givens bulge chase.
+ * These are the implicit restarts of the Arnoldi method. */
+int fv_host_shift_steps(int m, double* H, double* Q, int nshift, const double* sr,
+                        const double* si);
+
+/* Float-float conversions used by the mixed-precision SIMPLE loop:
+ * hi = nearest float to in, lo = nearest float to in - hi, joined = the
+ * float64 of hi + lo, rounded = nearest float (any output may be NULL). */
+int fv_host_ff_convert(int64_t n, const double* in, float* hi, float* lo, double* joined,
+                       float* rounded);
+
+/* Float-float arithmetic check: out = (a + b) * c, operands as (hi, lo) pairs. */
+int fv_host_ff_arith(int64_t n, const float* a, const float* b, const float* c, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FVNS_HOST_H */

@@ -47,6 +47,8 @@ _SIGS = {
     "fv_launch_count": (ctypes.c_int64, []),
     "fv_host_hess_eigenvalues": (_I, [_I, _P, _P, _P]),
     "fv_host_shift_steps": (_I, [_I, _P, _P, _I, _P, _P]),
+    "fv_host_ff_convert": (_I, [ctypes.c_int64, _P, _P, _P, _P, _P]),
+    "fv_host_ff_arith": (_I, [ctypes.c_int64, _P, _P, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)

@@ -10,6 +10,7 @@
 #include <complex>
 #include <vector>
 
+#include "fv_ff.cuh"
 #include "fv_internal.cuh"
 
 namespace fv {
@@ -234,6 +235,33 @@ extern "C" int fv_host_shift_steps(int m, double* H, double* Q, int nshift, cons
     } else {
       fv::single_shift_step(m, H, Q, sr[i]);
     }
+  }
+  return FV_OK;
+}
+
+// Float-float conversions of the mixed-precision path, host build of the
+// same integer routines the kernels use (for CPU tests).
+extern "C" int fv_host_ff_convert(int64_t n, const double* in, float* hi, float* lo,
+                                  double* joined, float* rounded) {
+  if (n < 0 || !in) return FV_EINVAL;
+  for (int64_t i = 0; i < n; ++i) {
+    const fv::ff s = fv::f64_split(in[i]);
+    if (hi) hi[i] = s.hi;
+    if (lo) lo[i] = s.lo;
+    if (joined) joined[i] = fv::ff_join(s.hi, s.lo);
+    if (rounded) rounded[i] = fv::f64_round_f32(in[i]);
+  }
+  return FV_OK;
+}
+
+// ff arithmetic on the host: out = (a + b) * c with a, b, c given as (hi, lo)
+extern "C" int fv_host_ff_arith(int64_t n, const float* a, const float* b, const float* c,
+                                float* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    const fv::ff x{a[2 * i], a[2 * i + 1]}, y{b[2 * i], b[2 * i + 1]}, z{c[2 * i], c[2 * i + 1]};
+    const fv::ff r = fv::ff_mul(fv::ff_add(x, y), z);
+    out[2 * i] = r.hi;
+    out[2 * i + 1] = r.lo;
   }
   return FV_OK;
 }

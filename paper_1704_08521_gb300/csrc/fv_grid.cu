@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 
+#include "fv_ff.cuh"
 #include "fv_internal.cuh"
 
 namespace fv {
@@ -254,6 +255,36 @@ static fv_status build(fv_grid* g) {
   for (int i = 0; i < 3; ++i) FV_TRY(alloc(g, (void**)&g->vel_buf[i], g->nvel * sizeof(double)));
   for (int i = 0; i < 3; ++i) FV_TRY(alloc(g, (void**)&g->cell_buf[i], g->ncell * sizeof(double)));
   for (int i = 0; i < 2; ++i) FV_TRY(alloc(g, &g->tpf_buf[i], g->ncell * sizeof(double)));
+  // mixed-precision workspace
+  FV_TRY(alloc(g, (void**)&g->U32, g->nvel * sizeof(float)));
+  FV_TRY(alloc(g, (void**)&g->x32, g->nvel * sizeof(float)));
+  FV_TRY(alloc(g, (void**)&g->w32, g->nvel * sizeof(float)));
+  for (int i = 0; i < 2; ++i) FV_TRY(alloc(g, (void**)&g->vff[i], g->nvel * sizeof(float2)));
+  FV_TRY(alloc(g, (void**)&g->pff, g->ncell * sizeof(float2)));
+  FV_TRY(alloc(g, (void**)&g->r32, g->ncell * sizeof(float)));
+  FV_TRY(alloc(g, (void**)&g->phi32, g->ncell * sizeof(float)));
+  {
+    size_t tot = 0;
+    for (int d = 0; d < 3; ++d) tot += g->n[d];
+    std::vector<float2> h(tot);
+    size_t off[3], o = 0;
+    for (int d = 0; d < 3; ++d) {
+      off[d] = o;
+      for (int m = 0; m < g->n[d]; ++m) {
+        const ff s = f64_split(1.0 / g->h_dx[d][m]);
+        h[o + m] = make_float2(s.hi, s.lo);
+      }
+      o += g->n[d];
+    }
+    FV_TRY(alloc(g, &g->d_met_ff, tot * sizeof(float2)));
+    FV_CUDA(cudaMemcpy(g->d_met_ff, h.data(), tot * sizeof(float2), cudaMemcpyHostToDevice));
+    for (int d = 0; d < 3; ++d) {
+      g->met_ff.n[d] = g->n[d];
+      g->met_ff.idc[d] = g->met_f.idc[d];
+      g->met_ff.idx[d] = (const float2*)g->d_met_ff + off[d];
+    }
+    g->met_ff.ncell = g->ncell;
+  }
   FV_TRY(alloc(g, (void**)&g->d_scal, kScalars * sizeof(double)));
   g->part_len = 4096 * 130;
   FV_TRY(alloc(g, (void**)&g->d_part, g->part_len * sizeof(double)));
@@ -351,7 +382,8 @@ void fv_grid_destroy(fv_grid* g) {
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   void* ptrs[] = {g->d_met_d, g->d_met_f, g->d_tpf_d, g->d_tpf_f, g->vel_buf[0], g->vel_buf[1],
                   g->vel_buf[2], g->cell_buf[0], g->cell_buf[1], g->cell_buf[2], g->tpf_buf[0],
-                  g->tpf_buf[1], g->d_scal, g->d_part, g->kry, g->kry_small};
+                  g->tpf_buf[1], g->d_scal, g->d_part, g->kry, g->kry_small, g->U32, g->x32,
+                  g->w32, g->vff[0], g->vff[1], g->pff, g->r32, g->phi32, g->d_met_ff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_scal) cudaFreeHost(g->h_scal);

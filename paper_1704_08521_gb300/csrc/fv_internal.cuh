@@ -57,6 +57,14 @@ struct AxisBasis {
   std::vector<double> Einv;    // n x n row-major: rhat[a] = sum_m Einv[a][m] r[m]
 };
 
+// float32 metrics plus the float-float 1/dx of the mixed SIMPLE loop
+struct MetFF {
+  int n[3];
+  int64_t ncell;
+  const float* idc[3];
+  const float2* idx[3];
+};
+
 template <typename T>
 struct TpfDev {
   int n[3];
@@ -99,6 +107,17 @@ struct fv_grid {
   double* h_scal = nullptr;      // pinned host mirror of d_scal
   int64_t ws_bytes = 0;
 
+  // mixed-precision workspace (float32 operands, float-float SIMPLE state)
+  float* U32 = nullptr;          // n_vel
+  float* x32 = nullptr;          // n_vel
+  float* w32 = nullptr;          // n_vel
+  float2* vff[2] = {nullptr, nullptr};   // n_vel each
+  float2* pff = nullptr;         // n_cell
+  float* r32 = nullptr;          // n_cell
+  float* phi32 = nullptr;        // n_cell
+  void* d_met_ff = nullptr;      // float-float 1/dx per axis
+  fv::MetFF met_ff;
+
   // optional per-kernel-class event timing
   mutable bool prof_on = false;
   mutable std::vector<cudaEvent_t> ev_pool;
@@ -118,6 +137,8 @@ enum {
   S_PHI_MAX = 0,   // max |phi| of the last SIMPLE pass (as uint64 bits)
   S_DIV_MAX = 1,   // max |D v|
   S_NAN = 2,       // nonzero when a NaN was seen
+  S_PHI_MAX_F = 3, // float max |phi| (bits in the low word) of the mixed loop
+  S_DIV_MAX_F = 4, // float max |D v| of the mixed loop
   S_RED = 8        // start of general reduction results (56 slots)
 };
 constexpr int kScalars = 64;
@@ -148,8 +169,23 @@ fv_status launch_correct_div(const fv_grid* g, const double* vin, double* vout,
                              double omega);
 fv_status launch_zero_walls(const fv_grid* g, double* v);
 
+// mixed-precision path (fv_mixed.cu)
+fv_status launch_momentum_f32(const fv_grid* g, const float* U32, const float* v32, float* out,
+                              double shift);
+fv_status launch_round_f32(const fv_grid* g, const double* in, float* out, int64_t n);
+fv_status launch_div_f32(const fv_grid* g, const float* w32, float* r32);
+// one float-float SIMPLE pass; first: vin is the float32 w, p starts at 0
+fv_status launch_correct_ff(const fv_grid* g, bool first, const void* vin, float2* vout,
+                            const float* phi, float2* p, float* r, double omega);
+// out = hi + lo (- sigma * x) as float64; p_out = p_ff
+fv_status launch_join_ff(const fv_grid* g, const float2* v, const double* x, double sigma,
+                         double* out, int64_t n);
+fv_status launch_join_ff_cells(const fv_grid* g, const float2* p, double* out);
+fv_status launch_widen_f32(const fv_grid* g, const float* in, double* out, int64_t n);
+
 // tensor-product pressure solve: phi = (D G)^+ r ; phi is float or double
 fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec);
+fv_status tpf_solve_f32(const fv_grid* g, const float* r, float* phi);
 
 // vector kernels (weighted inner products, Gram-Schmidt)
 fv_status vec_dots(const fv_grid* g, const double* V, int64_t ldv, int nvec, const double* w,

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fv_ff.cuh"
 #include "fv_internal.cuh"
 
 namespace fv {
@@ -278,7 +279,8 @@ struct SimpleResult {
 };
 
 static fv_status simple_loop(const fv_grid* g, double* cur, double* spare, double* out, double* p,
-                             double eps, int max_pass, int prec, double omega, SimpleResult* res) {
+                             double eps, int max_pass, int prec, double omega, SimpleResult* res,
+                             double div_abs = 0.0) {
   double* r = g->cell_buf[0];
   void* phi = (void*)g->cell_buf[1];
   FV_TRY(reset_scalars(g));
@@ -300,10 +302,58 @@ static fv_status simple_loop(const fv_grid* g, double* cur, double* spare, doubl
     if (h[S_NAN] != 0.0) { set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN; }
     if (pass == 1) phi1 = ph;
     res->phi_first = phi1;
+    const double prev = res->phi_last;
     res->phi_last = ph;
-    if (ph == 0.0 || ph <= eps * phi1) { st = FV_OK; break; }
+    if (ph == 0.0 || ph <= eps * phi1 || res->div_max <= div_abs) { st = FV_OK; break; }
+    // round-off floor: the corrections stopped shrinking at a level far
+    // below the first one (the requested eps lies under the floor of the
+    // arithmetic); the fields are as divergence-free as they can get
+    if (pass >= 3 && ph > 0.25 * prev && ph <= 1e-9 * phi1) { st = FV_OK; break; }
   }
   if (cur != out) FV_CUDA(cudaMemcpyAsync(out, cur, g->nvel * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  if (st != FV_OK) set_error("SIMPLE loop reached max_pass");
+  return st;
+}
+
+static float slot_float(const double* h, int slot) {
+  float f;
+  std::memcpy(&f, (const char*)(h + slot), sizeof(float));
+  return f;
+}
+
+// Mixed-precision SIMPLE loop on the float-float state, starting from the
+// float32 predictor in g->w32 whose divergence is in g->r32.  Writes
+// out = v - sigma x (float64) and p_out (optional).
+static fv_status simple_loop_ff(const fv_grid* g, double* out, double* p_out, const double* x,
+                                double sigma, double eps, int max_pass, double omega,
+                                SimpleResult* res) {
+  const void* cur = g->w32;
+  int nxt = 0;
+  double h[kScalars];
+  double phi1 = 0.0;
+  res->passes = 0;
+  res->phi_last = 0.0;
+  fv_status st = FV_ENOCONV;
+  for (int pass = 1; pass <= max_pass; ++pass) {
+    FV_TRY(tpf_solve_f32(g, g->r32, g->phi32));
+    FV_TRY(reset_scalars(g));
+    FV_TRY(launch_correct_ff(g, pass == 1, cur, g->vff[nxt], g->phi32, g->pff, g->r32, omega));
+    cur = g->vff[nxt];
+    nxt ^= 1;
+    FV_TRY(fetch_scalars(g, h));
+    res->passes = pass;
+    if (h[S_NAN] != 0.0) { set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN; }
+    const double ph = slot_float(h, S_PHI_MAX_F);
+    res->div_max = slot_float(h, S_DIV_MAX_F);
+    if (pass == 1) phi1 = ph;
+    res->phi_first = phi1;
+    const double prev = res->phi_last;
+    res->phi_last = ph;
+    if (ph == 0.0 || ph <= eps * phi1) { st = FV_OK; break; }
+    if (pass >= 3 && ph > 0.25 * prev && ph <= 1e-9 * phi1) { st = FV_OK; break; }
+  }
+  FV_TRY(launch_join_ff(g, (const float2*)cur, sigma != 0.0 ? x : nullptr, sigma, out, g->nvel));
+  if (p_out) FV_TRY(launch_join_ff_cells(g, g->pff, p_out));
   if (st != FV_OK) set_error("SIMPLE loop reached max_pass");
   return st;
 }
@@ -313,6 +363,13 @@ static fv_status simple_loop(const fv_grid* g, double* cur, double* spare, doubl
 static fv_status krylov_apply(const fv_grid* g, const double* U, const double* x, double* out,
                               double* p, double sigma, int prec, double eps, int max_pass,
                               double omega, SimpleResult* res) {
+  if (prec == FV_MIXED) {
+    FV_TRY(launch_round_f32(g, U, g->U32, g->nvel));
+    FV_TRY(launch_round_f32(g, x, g->x32, g->nvel));
+    FV_TRY(launch_momentum_f32(g, g->U32, g->x32, g->w32, sigma));
+    FV_TRY(launch_div_f32(g, g->w32, g->r32));
+    return simple_loop_ff(g, out, p, x, sigma, eps, max_pass, omega, res);
+  }
   FV_TRY(launch_momentum_jac(g, U, x, out, prec, sigma));
   fv_status s = simple_loop(g, out, g->vel_buf[0], out, p, eps, max_pass, prec, omega, res);
   if (s != FV_OK) return s;
@@ -320,10 +377,18 @@ static fv_status krylov_apply(const fv_grid* g, const double* U, const double* x
   return FV_OK;
 }
 
-// Project x in place onto divergence-free fields (p: optional pressure out).
+static fv_status maxabs_host(const fv_grid* g, int64_t n, const double* x, double* out, bool* nan);
+
+// Project x in place onto divergence-free fields (p: optional pressure out),
+// until the divergence is at round-off level for the size of x.
 static fv_status project_inplace(const fv_grid* g, double* x, double* p, int prec, double eps,
                                  SimpleResult* res) {
-  return simple_loop(g, x, g->vel_buf[0], x, p, eps, 200, prec, 1.0, res);
+  double xmax;
+  FV_TRY(maxabs_host(g, g->nvel, x, &xmax, nullptr));
+  double hmin = 1.0;
+  for (int d = 0; d < 3; ++d)
+    for (double h : g->h_dx[d]) hmin = std::min(hmin, h);
+  return simple_loop(g, x, g->vel_buf[0], x, p, eps, 200, prec, 1.0, res, 1e-14 * xmax / hmin);
 }
 
 static fv_status ensure_krylov(fv_grid* g, int cols) {

@@ -1,0 +1,208 @@
+// Mixed-precision SIMPLE loop (Section 3, the algorithm after Eq. 10) laid
+// out for GB300, whose FP64 pipes run at ~1/70 of the FP32 rate:
+//   * J.v and the pressure-correction transforms in float32;
+//   * the velocity/pressure state of the loop as float-float pairs
+//     (hi + lo, ~48 bits), updated and differenced on the FP32 pipes, so the
+//     divergence that drives the next correction is computed far below
+//     float32 round-off (the defect-correction residual);
+//   * float64 only at the API boundary, converted with integer operations.
+// Each pass reads/writes every field once: the correction of the cell's own
+// faces, the on-the-fly correction of its high faces and the new divergence
+// are fused in one kernel (ping-pong buffers, no read-after-write hazard).
+#include "fv_ff.cuh"
+#include "fv_internal.cuh"
+
+namespace fv {
+
+namespace {
+
+__device__ __forceinline__ float2 to2(ff a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ ff of2(float2 a) { return {a.x, a.y}; }
+
+__device__ __forceinline__ float block_maxf(float v) {
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = (lane < nw) ? red[lane] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+__global__ void k_round_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = f64_round_f32(__ldg(in + e));
+}
+
+__global__ void k_widen_f32(const float* __restrict__ in, double* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = f32_to_f64(__ldg(in + e));
+}
+
+// D w in float32 (first residual of the loop; w holds float32 values).
+__global__ void __launch_bounds__(256) k_div_f32(MetFF m, const float* __restrict__ w,
+                                                 float* __restrict__ r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  if (i >= m.n[0]) return;
+  const int64_t nx = m.n[0], nxy = nx * m.n[1], nc = m.ncell;
+  const int64_t base = ((int64_t)k * m.n[1] + j) * nx + i;
+  const float u0 = (i > 0) ? w[base] : 0.f;
+  const float u1 = (i + 1 < m.n[0]) ? w[base + 1] : 0.f;
+  const float v0 = (j > 0) ? w[nc + base] : 0.f;
+  const float v1 = (j + 1 < m.n[1]) ? w[nc + base + nx] : 0.f;
+  const float w0 = (k > 0) ? w[2 * nc + base] : 0.f;
+  const float w1 = (k + 1 < m.n[2]) ? w[2 * nc + base + nxy] : 0.f;
+  r[base] = (u1 - u0) * m.idx[0][i].x + (v1 - v0) * m.idx[1][j].x + (w1 - w0) * m.idx[2][k].x;
+}
+
+// One pass: v_out = v_in - omega G phi (own faces), p += omega phi, and
+// r = D v_out in float-float arithmetic, rounded to float32 for the next
+// pressure-correction solve.  FIRST: v_in is the float32 predictor w.
+template <bool FIRST>
+__global__ void __launch_bounds__(256) k_correct_ff(MetFF m, const void* __restrict__ vin_,
+                                                    float2* __restrict__ vout,
+                                                    const float* __restrict__ phi,
+                                                    float2* __restrict__ p, float* __restrict__ r,
+                                                    float omega, double* scal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  float aphi = 0.f, adiv = 0.f;
+  if (i < m.n[0]) {
+    const int pos[3] = {i, j, k};
+    const int64_t st[3] = {1, (int64_t)m.n[0], (int64_t)m.n[0] * m.n[1]};
+    const int64_t nc = m.ncell;
+    const int64_t base = ((int64_t)k * m.n[1] + j) * m.n[0] + i;
+    const float* w32 = (const float*)vin_;
+    const float2* vin = (const float2*)vin_;
+    auto load = [&](int64_t e) -> ff {
+      if (FIRST) return {__ldg(w32 + e), 0.f};
+      return of2(__ldg(vin + e));
+    };
+    const float f0 = __ldg(phi + base);
+    ff dv = {0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int q = pos[c];
+      ff lo = {0.f, 0.f}, hi = {0.f, 0.f};
+      if (q > 0) {
+        const float g = (f0 - __ldg(phi + base - st[c])) * m.idc[c][q];
+        lo = ff_add_f(load(c * nc + base), -omega * g);
+      }
+      vout[c * nc + base] = to2(lo);
+      if (q + 1 < m.n[c]) {
+        const float g = (__ldg(phi + base + st[c]) - f0) * m.idc[c][q + 1];
+        hi = ff_add_f(load(c * nc + base + st[c]), -omega * g);
+      }
+      dv = ff_add(dv, ff_mul(ff_sub(hi, lo), of2(m.idx[c][q])));
+    }
+    r[base] = dv.hi;
+    if (FIRST) p[base] = make_float2(omega * f0, 0.f);
+    else p[base] = to2(ff_add_f(of2(p[base]), omega * f0));
+    aphi = fabsf(f0);
+    adiv = fabsf(dv.hi);
+    if (!(aphi <= 3e38f) || !(adiv <= 3e38f)) {
+      scal[S_NAN] = 1.0;
+      aphi = adiv = 0.f;
+    }
+  }
+  aphi = block_maxf(aphi);
+  adiv = block_maxf(adiv);
+  if (threadIdx.x == 0) {
+    atomicMax((unsigned*)(scal + S_PHI_MAX_F), __float_as_uint(aphi));
+    atomicMax((unsigned*)(scal + S_DIV_MAX_F), __float_as_uint(adiv));
+  }
+}
+
+__global__ void k_join_ff(const float2* __restrict__ v, const double* __restrict__ x, float sigma,
+                          double* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    ff a = of2(__ldg(v + e));
+    if (x) a = ff_sub(a, ff_mul_f(f64_split(__ldg(x + e)), sigma));
+    out[e] = ff_join(a.hi, a.lo);
+  }
+}
+
+inline unsigned grid1d(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+inline dim3 cell_grid(const fv_grid* g, int bx) {
+  return dim3((g->n[0] + bx - 1) / bx, g->n[1], g->n[2]);
+}
+
+inline int block_x(const fv_grid* g) {
+  return g->n[0] >= 128 ? 128 : (g->n[0] >= 64 ? 64 : 32);
+}
+
+}  // namespace
+
+fv_status launch_round_f32(const fv_grid* g, const double* in, float* out, int64_t n) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_round_f32<<<grid1d(n), 256, 0, g->stream>>>(in, out, n);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_widen_f32(const fv_grid* g, const float* in, double* out, int64_t n) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_widen_f32<<<grid1d(n), 256, 0, g->stream>>>(in, out, n);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_div_f32(const fv_grid* g, const float* w32, float* r32) {
+  const int bx = block_x(g);
+  {
+    LaunchScope ls_(g, FV_K_DIVERGENCE);
+    k_div_f32<<<cell_grid(g, bx), bx, 0, g->stream>>>(g->met_ff, w32, r32);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_correct_ff(const fv_grid* g, bool first, const void* vin, float2* vout,
+                            const float* phi, float2* p, float* r, double omega) {
+  const int bx = block_x(g);
+  {
+    LaunchScope ls_(g, FV_K_CORRECT);
+    if (first)
+      k_correct_ff<true><<<cell_grid(g, bx), bx, 0, g->stream>>>(g->met_ff, vin, vout, phi, p, r,
+                                                                 float(omega), g->d_scal);
+    else
+      k_correct_ff<false><<<cell_grid(g, bx), bx, 0, g->stream>>>(g->met_ff, vin, vout, phi, p, r,
+                                                                  float(omega), g->d_scal);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_join_ff(const fv_grid* g, const float2* v, const double* x, double sigma,
+                         double* out, int64_t n) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_join_ff<<<grid1d(n), 256, 0, g->stream>>>(v, x, float(sigma), out, n);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_join_ff_cells(const fv_grid* g, const float2* p, double* out) {
+  return launch_join_ff(g, p, nullptr, 0.0, out, g->ncell);
+}
+
+}  // namespace fv

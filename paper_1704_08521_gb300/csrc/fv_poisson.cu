@@ -167,11 +167,11 @@ fv_status run_left(const fv_grid* g, int axis, const T* M, const TI* in, TO* out
   return FV_OK;
 }
 
-template <typename T, typename TO>
-fv_status tpf_run(const fv_grid* g, const TpfDev<T>& tp, const double* r, TO* phi) {
+template <typename T, typename TI, typename TO>
+fv_status tpf_run(const fv_grid* g, const TpfDev<T>& tp, const TI* r, TO* phi) {
   T* a = (T*)g->tpf_buf[0];
   T* b = (T*)g->tpf_buf[1];
-  FV_TRY((run_right<T, double, T>(g, tp.Einv[0], r, a)));              // x forward
+  FV_TRY((run_right<T, TI, T>(g, tp.Einv[0], r, a)));                  // x forward
   FV_TRY((run_left<T, T, T, false>(g, 1, tp.Einv[1], a, b, tp)));      // y forward
   FV_TRY((run_left<T, T, T, true>(g, 2, tp.Einv[2], b, a, tp)));       // z forward + scale
   FV_TRY((run_left<T, T, T, false>(g, 2, tp.E[2], a, b, tp)));         // z inverse
@@ -183,8 +183,12 @@ fv_status tpf_run(const fv_grid* g, const TpfDev<T>& tp, const double* r, TO* ph
 }  // namespace
 
 fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec) {
-  if (prec == FV_MIXED) return tpf_run<float, float>(g, g->tpf_f, r, (float*)phi);
-  return tpf_run<double, double>(g, g->tpf_d, r, (double*)phi);
+  if (prec == FV_MIXED) return tpf_run<float, double, float>(g, g->tpf_f, r, (float*)phi);
+  return tpf_run<double, double, double>(g, g->tpf_d, r, (double*)phi);
+}
+
+fv_status tpf_solve_f32(const fv_grid* g, const float* r, float* phi) {
+  return tpf_run<float, float, float>(g, g->tpf_f, r, phi);
 }
 
 }  // namespace fv
@@ -196,6 +200,7 @@ extern "C" fv_status fv_pressure_solve(const fv_grid* g, const double* r, double
   if (prec != FV_FP64 && prec != FV_MIXED) { set_error("fv_pressure_solve: bad prec"); return FV_EINVAL; }
   if (prec == FV_FP64) return tpf_solve(g, r, phi, FV_FP64);
   // mixed: float32 solve, widened into phi
-  FV_TRY(tpf_solve(g, r, g->cell_buf[2], FV_MIXED));
-  return widen_float(g, (const float*)g->cell_buf[2], phi, g->ncell);
+  FV_TRY(launch_round_f32(g, r, g->r32, g->ncell));
+  FV_TRY(tpf_solve_f32(g, g->r32, g->phi32));
+  return launch_widen_f32(g, g->phi32, phi, g->ncell);
 }

@@ -9,28 +9,38 @@
 //   convection : flux = (transport velocity) x (transported velocity), each
 //                linearly interpolated (distance weighted) to the control-
 //                volume face; wall fluxes vanish (zero normal velocity).
+#include "fv_ff.cuh"
 #include "fv_internal.cuh"
 
 namespace fv {
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ T ld(const double* __restrict__ p, int64_t i) {
-  return T(__ldg(p + i));
+// load an input value in the arithmetic type T; double -> float goes through
+// the integer rounding of fv_ff.cuh, not the (slow on GB300) FP64 converter
+template <typename T, typename TI>
+__device__ __forceinline__ T ld(const TI* __restrict__ p, int64_t i) {
+  if constexpr (sizeof(T) == sizeof(TI)) return __ldg(p + i);
+  else return T(__ldg(p + i));
+}
+
+template <typename T, typename TO>
+__device__ __forceinline__ TO to_out(T v) {
+  if constexpr (sizeof(T) == 4 && sizeof(TO) == 8) return f32_to_f64(v);
+  else return TO(v);
 }
 
 // Momentum balance of component C at the face owned by cell (i, j, k).
 // JAC: (1/Re) Lap v - div(U (x) v) - div(v (x) U) + shift v   (homogeneous walls)
 // else: (1/Re) Lap U - div(U (x) U)                            (lid wall values)
-template <typename T, int C, bool JAC>
-__device__ __forceinline__ T momentum_face(const Met<T>& m, const double* __restrict__ U,
-                                           const double* __restrict__ V, int64_t base,
+template <typename T, int C, bool JAC, typename TI>
+__device__ __forceinline__ T momentum_face(const Met<T>& m, const TI* __restrict__ U,
+                                           const TI* __restrict__ V, int64_t base,
                                            const int (&pos)[3], const int64_t (&st)[3],
                                            T inv_re, T lid_hi, T shift) {
   const int64_t nc = m.ncell;
-  const double* Uc = U + C * nc;
-  const double* Qc = (JAC ? V : U) + C * nc;
+  const TI* Uc = U + C * nc;
+  const TI* Qc = (JAC ? V : U) + C * nc;
   const int f = pos[C];
   const int nC = m.n[C];
 
@@ -70,8 +80,8 @@ __device__ __forceinline__ T momentum_face(const Met<T>& m, const double* __rest
     // convective fluxes through the d-faces e (low) and e+1 (high) of the
     // C-control volume; the transport velocity a_d is interpolated along C
     // from the centres f-1, f; the transported b_C along d from e-1, e.
-    const double* Ud = U + d * nc;
-    const double* Vd = V + d * nc;
+    const TI* Ud = U + d * nc;
+    const TI* Vd = V + d * nc;
     const T thc = m.th[C][f];
     T Flo = T(0), Fhi = T(0);
     if (e > 0) {
@@ -109,11 +119,11 @@ __device__ __forceinline__ T momentum_face(const Met<T>& m, const double* __rest
   return out;
 }
 
-template <typename T, bool JAC>
-__global__ void __launch_bounds__(256) k_momentum(Met<T> m, const double* __restrict__ U,
-                                                  const double* __restrict__ V,
+template <typename T, bool JAC, typename TI, typename TO>
+__global__ void __launch_bounds__(256) k_momentum(Met<T> m, const TI* __restrict__ U,
+                                                  const TI* __restrict__ V,
                                                   const double* __restrict__ P,
-                                                  double* __restrict__ out, T inv_re, T lid_u,
+                                                  TO* __restrict__ out, T inv_re, T lid_u,
                                                   T lid_v, T shift) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
@@ -127,28 +137,28 @@ __global__ void __launch_bounds__(256) k_momentum(Met<T> m, const double* __rest
   {
     T r = T(0);
     if (i > 0) {
-      r = momentum_face<T, 0, JAC>(m, U, V, base, pos, st, inv_re, lid_u, shift);
+      r = momentum_face<T, 0, JAC, TI>(m, U, V, base, pos, st, inv_re, lid_u, shift);
       if (!JAC) r -= T(__ldg(P + base) - __ldg(P + base - 1)) * m.idc[0][i];
     }
-    out[base] = double(r);
+    out[base] = to_out<T, TO>(r);
   }
   // v (y-faces)
   {
     T r = T(0);
     if (j > 0) {
-      r = momentum_face<T, 1, JAC>(m, U, V, base, pos, st, inv_re, lid_v, shift);
+      r = momentum_face<T, 1, JAC, TI>(m, U, V, base, pos, st, inv_re, lid_v, shift);
       if (!JAC) r -= T(__ldg(P + base) - __ldg(P + base - st[1])) * m.idc[1][j];
     }
-    out[nc + base] = double(r);
+    out[nc + base] = to_out<T, TO>(r);
   }
   // w (z-faces)
   {
     T r = T(0);
     if (k > 0) {
-      r = momentum_face<T, 2, JAC>(m, U, V, base, pos, st, inv_re, T(0), shift);
+      r = momentum_face<T, 2, JAC, TI>(m, U, V, base, pos, st, inv_re, T(0), shift);
       if (!JAC) r -= T(__ldg(P + base) - __ldg(P + base - st[2])) * m.idc[2][k];
     }
-    out[2 * nc + base] = double(r);
+    out[2 * nc + base] = to_out<T, TO>(r);
   }
 }
 
@@ -281,17 +291,33 @@ fv_status launch_momentum_jac(const fv_grid* g, const double* U, const double* v
                               int prec, double shift) {
   const int bx = block_x(g);
   if (prec == FV_MIXED) {
+    // float32 operands (rounded once, integer conversion), float32 J.v,
+    // exact widening of the result
+    FV_TRY(launch_round_f32(g, U, g->U32, g->nvel));
+    FV_TRY(launch_round_f32(g, v, g->x32, g->nvel));
     {
       LaunchScope ls_(g, FV_K_MOMENTUM);
-      k_momentum<float, true><<<cell_grid(g, bx), bx, 0, g->stream>>>(
-          g->met_f, U, v, nullptr, out, float(1.0 / g->re), 0.f, 0.f, float(shift));
+      k_momentum<float, true, float, double><<<cell_grid(g, bx), bx, 0, g->stream>>>(
+          g->met_f, g->U32, g->x32, nullptr, out, float(1.0 / g->re), 0.f, 0.f, float(shift));
     }
   } else {
     {
       LaunchScope ls_(g, FV_K_MOMENTUM);
-      k_momentum<double, true><<<cell_grid(g, bx), bx, 0, g->stream>>>(
+      k_momentum<double, true, double, double><<<cell_grid(g, bx), bx, 0, g->stream>>>(
           g->met_d, U, v, nullptr, out, 1.0 / g->re, 0.0, 0.0, shift);
     }
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_momentum_f32(const fv_grid* g, const float* U32, const float* v32, float* out,
+                              double shift) {
+  const int bx = block_x(g);
+  {
+    LaunchScope ls_(g, FV_K_MOMENTUM);
+    k_momentum<float, true, float, float><<<cell_grid(g, bx), bx, 0, g->stream>>>(
+        g->met_f, U32, v32, nullptr, out, float(1.0 / g->re), 0.f, 0.f, float(shift));
   }
   FV_CHECK_LAUNCH();
   return FV_OK;
@@ -302,7 +328,7 @@ fv_status launch_residual(const fv_grid* g, const double* U, const double* P, do
   const int bx = block_x(g);
   {
     LaunchScope ls_(g, FV_K_MOMENTUM);
-    k_momentum<double, false><<<cell_grid(g, bx), bx, 0, g->stream>>>(
+    k_momentum<double, false, double, double><<<cell_grid(g, bx), bx, 0, g->stream>>>(
         g->met_d, U, U, P, Fm, 1.0 / g->re, std::cos(g->alpha), std::sin(g->alpha), 0.0);
   }
   FV_CHECK_LAUNCH();

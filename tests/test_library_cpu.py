@@ -81,3 +81,46 @@ def test_exact_shifts_deflate_and_preserve_similarity(lib):
     assert np.abs(Q[m - 1, :k - 1]).max() < 1e-12
     assert abs(Hs[k, k - 1]) < 1e-6 * np.abs(H).max()
     np.testing.assert_allclose(np.sort_complex(np.linalg.eigvals(Hs[:k, :k])), np.sort_complex(lam[:k]), atol=1e-7)
+
+
+def test_ff_conversions_match_ieee(lib):
+    # integer-only double <-> float-float conversions of the mixed path
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000),
+                        [0.0, -0.0, 1.0, -1.0, 1e-40, 3.4e38, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24,
+                         np.pi, -np.e, 1e-30, 2.0 ** -126]])
+    n = x.size
+    hi = np.zeros(n, np.float32); lo = np.zeros(n, np.float32)
+    jo = np.zeros(n); ro = np.zeros(n, np.float32)
+    assert lib.fv_host_ff_convert(n, x.ctypes.data, hi.ctypes.data, lo.ctypes.data,
+                                  jo.ctypes.data, ro.ctypes.data) == 0
+    normal = np.abs(x) >= 2.0 ** -126
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float32)
+    assert np.array_equal(ro[normal], ref[normal])                  # round to nearest even
+    assert np.array_equal(hi, ro)
+    big = np.abs(x) > 1e-20
+    np.testing.assert_allclose(lo[big].astype(np.float64), (x - hi.astype(np.float64))[big],
+                               rtol=2.0 ** -23, atol=0)
+    np.testing.assert_allclose(jo[big], x[big], rtol=2.0 ** -47, atol=0)
+    # joining the pair reproduces hi + lo exactly when it is representable
+    pair = hi.astype(np.float64) + lo.astype(np.float64)
+    np.testing.assert_array_equal(jo[big], pair[big])
+
+
+def test_ff_arithmetic_48_bits(lib):
+    rng = np.random.default_rng(12)
+    n = 5000
+    def ffpair(v):
+        h = v.astype(np.float32)
+        l = (v - h.astype(np.float64)).astype(np.float32)
+        return np.ascontiguousarray(np.stack([h, l], 1).ravel()), h.astype(np.float64) + l
+    a, av = ffpair(rng.standard_normal(n))
+    b, bv = ffpair(rng.standard_normal(n) * 0.999)
+    c, cv = ffpair(rng.standard_normal(n) * 3.0)
+    out = np.zeros(2 * n, np.float32)
+    lib.fv_host_ff_arith(n, a.ctypes.data, b.ctypes.data, c.ctypes.data, out.ctypes.data)
+    got = out[0::2].astype(np.float64) + out[1::2]
+    ref = (av + bv) * cv
+    scale = (np.abs(av) + np.abs(bv)) * np.abs(cv)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -44 * scale)

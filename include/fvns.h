@@ -188,6 +188,23 @@ fv_status fv_dot_w(const fv_grid* g, const double* a, const double* b, double* o
  * (Neumann) by the tensor-product factorisation; prec as above. */
 fv_status fv_pressure_solve(const fv_grid* g, const double* r, double* phi, int prec);
 
+/* Allocation-free variant of fv_pressure_solve (prec = FV_MIXED) for callers
+ * that cannot allocate device memory -- inside someone else's memory pool,
+ * during a CUDA graph capture, or without access to an allocator.  The paper
+ * has no counterpart: this is a property of the library, not of the method.
+ * It needs no grid handle: nx, ny, nz (each in [4, 128], nx*ny*nz <=
+ * 1048576) and map describe the grid; r[n_cell] (device, float64) is the
+ * right-hand side, phi[n_cell] (device, float64) receives the zero-mean
+ * solution of D G phi = r, work is queued on cuda_stream.  All scratch
+ * (eigenbases and two float32 transform buffers, ~8.4 MB) lives in one
+ * fixed device array inside the library, allocated when the library is
+ * loaded and held by every GPU that loads it until the process exits.  The
+ * first call on a device looks up that array's device address (make it
+ * before any stream capture).  Sizes beyond the limits give FV_EINVAL.
+ * Calls share the array: calls that overlap on the GPU race on it. */
+fv_status fv_pressure_solve_noalloc(int nx, int ny, int nz, int map, const double* r,
+                                    double* phi, void* cuda_stream);
+
 /* ------------------------------------------------------- instrumentation --
  * Kernel classes timed by the optional per-grid profiler (CUDA events
  * recorded on the grid's stream around every launch of that class). */

@@ -189,6 +189,16 @@ def fv_pressure_solve(g, r, phi, prec="fp64"):
                                 PRECS.get(prec, prec)), "fv_pressure_solve")
 
 
+def fv_pressure_solve_noalloc(shape, map, r, phi, stream=None):
+    """Allocation-free float32 pressure-correction solve (see include/fvns.h)."""
+    nz, ny, nx = shape
+    n = nx * ny * nz
+    st = _stream() if stream is None else ctypes.c_void_p(stream)
+    check(lib.fv_pressure_solve_noalloc(nx, ny, nz, MAPS[map] if isinstance(map, str) else int(map),
+                                        _f64(r, n, "r"), _f64(phi, n, "phi"), st),
+          "fv_pressure_solve_noalloc")
+
+
 KERNEL_KINDS = ["momentum", "divergence", "correct", "tpf_x", "tpf_yz", "dots", "vector"]
 
 

@@ -42,6 +42,7 @@ _SIGS = {
     "arnoldi_leading": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P]),
     "fv_dot_w": (_I, [_P, _P, _P, _P]),
     "fv_pressure_solve": (_I, [_P, _P, _P, _I]),
+    "fv_pressure_solve_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P]),
     "fv_profile_enable": (_I, [_P, _I]),
     "fv_profile_read": (_I, [_P, _P, _P]),
     "fv_launch_count": (ctypes.c_int64, []),

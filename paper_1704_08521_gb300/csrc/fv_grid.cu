@@ -150,6 +150,19 @@ static bool axis_basis(const std::vector<double>& dx, const std::vector<double>&
   return true;
 }
 
+// Tensor-product tables of one axis with n cells and map `map`, on the host
+// (used by the allocation-free pressure solve).
+bool host_axis_tables(int n, int map, AxisBasis& B) {
+  const std::vector<double> x = map_faces(n, map);
+  std::vector<double> dx(n), xc(n), dc(n + 1);
+  for (int m = 0; m < n; ++m) dx[m] = x[m + 1] - x[m];
+  for (int m = 0; m < n; ++m) xc[m] = 0.5 * (x[m] + x[m + 1]);
+  dc[0] = 0.5 * dx[0];
+  for (int f = 1; f < n; ++f) dc[f] = xc[f] - xc[f - 1];
+  dc[n] = 0.5 * dx[n - 1];
+  return axis_basis(dx, dc, B);
+}
+
 template <typename T>
 static fv_status upload_metrics(fv_grid* g, void** dst, Met<T>& met) {
   // layout per axis: idx[n], idc[n+1], th[n+1], dx[n], dc[n+1]

@@ -210,6 +210,7 @@ double bits_to_double(double slot);
 // small dense linear algebra (host), used by the GMRES / Arnoldi drivers
 // H is m x m row-major upper Hessenberg.
 bool hess_eigenvalues(int m, const double* H, double* wr, double* wi);
+bool host_axis_tables(int n, int map, AxisBasis& B);
 void francis_double_step(int m, double* H, double* Q, double s, double t);
 void single_shift_step(int m, double* H, double* Q, double mu);
 // y (complex, m) with (H - theta I) y ~ 0, unit 2-norm

@@ -204,3 +204,120 @@ extern "C" fv_status fv_pressure_solve(const fv_grid* g, const double* r, double
   FV_TRY(tpf_solve_f32(g, g->r32, g->phi32));
   return launch_widen_f32(g, g->phi32, phi, g->ncell);
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free pressure-correction solve.
+//
+// Some callers cannot allocate device memory: code that runs inside a
+// memory pool it does not own, callers in the middle of a CUDA graph
+// capture (where cudaMalloc is not allowed), or embedded users whose
+// allocator is not reachable from this library.  For them
+// fv_pressure_solve_noalloc runs the float32 tensor-product solve with all
+// of its scratch (the per-axis eigenbases and the two transform buffers) in
+// one file-scope device array of fixed size, so it calls no cudaMalloc,
+// cudaFree or allocating library routine.  Limits: every dimension in
+// [4, kNaMaxDim] and nx*ny*nz <= kNaMaxCells.  The array is shared by every
+// call in the process: its contents are overwritten by each call (nothing in
+// it needs to start at zero: the tables and both buffers are fully written
+// before they are read), and calls that overlap on the GPU race on it.
+namespace fv {
+namespace {
+
+constexpr int kNaMaxDim = 128;
+constexpr int64_t kNaMaxCells = (int64_t)1 << 20;
+constexpr int64_t kNaTables = 3 * (2 * (int64_t)kNaMaxDim * kNaMaxDim + kNaMaxDim);
+constexpr int64_t kNaFloats = kNaTables + 2 * kNaMaxCells;
+
+static __device__ __align__(256) float g_na_scratch[kNaFloats];
+
+// device address of g_na_scratch per device, looked up once per device
+static float* g_na_ptr[64] = {nullptr};
+
+fv_status na_scratch_address(float** out) {
+  int dev = 0;
+  FV_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) { set_error("fv_pressure_solve_noalloc: device index out of range"); return FV_EINVAL; }
+  if (!g_na_ptr[dev]) {
+    void* p = nullptr;
+    FV_CUDA(cudaGetSymbolAddress(&p, g_na_scratch));
+    g_na_ptr[dev] = (float*)p;
+  }
+  *out = g_na_ptr[dev];
+  return FV_OK;
+}
+
+template <typename TI, typename TO>
+fv_status na_right(cudaStream_t st, int n, int64_t R, const float* M, const TI* in, TO* out) {
+  dim3 grid((unsigned)((R + TM - 1) / TM), (n + TN - 1) / TN, 1);
+  count_launch();
+  k_right<float, TI, TO><<<grid, 256, 0, st>>>(M, in, out, n, R);
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+template <bool SCALE>
+fv_status na_left(cudaStream_t st, int n, int64_t Q, int batch, const float* M, const float* in,
+                  float* out, const TpfDev<float>& tp) {
+  dim3 grid((unsigned)((Q + TN - 1) / TN), (n + TM - 1) / TM, batch);
+  count_launch();
+  k_left<float, float, float, SCALE><<<grid, 256, 0, st>>>(M, in, out, n, Q, tp);
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+}  // namespace
+
+}  // namespace fv
+
+extern "C" fv_status fv_pressure_solve_noalloc(int nx, int ny, int nz, int map, const double* r,
+                                               double* phi, void* cuda_stream) {
+  using namespace fv;
+  if (!r || !phi) { set_error("fv_pressure_solve_noalloc: NULL pointer"); return FV_EINVAL; }
+  if (map < 0 || map > 2) { set_error("fv_pressure_solve_noalloc: unknown map"); return FV_EINVAL; }
+  const int n[3] = {nx, ny, nz};
+  for (int d = 0; d < 3; ++d)
+    if (n[d] < 4 || n[d] > kNaMaxDim) {
+      set_error("fv_pressure_solve_noalloc: each dimension must be in [4, 128] (static scratch limit)");
+      return FV_EINVAL;
+    }
+  const int64_t ncell = (int64_t)nx * ny * nz;
+  if (ncell > kNaMaxCells) {
+    set_error("fv_pressure_solve_noalloc: nx*ny*nz must be <= 1048576 (static scratch limit)");
+    return FV_EINVAL;
+  }
+  float* base = nullptr;
+  FV_TRY(na_scratch_address(&base));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // tables: E, Einv, lam per axis, packed at the start of the scratch array
+  std::vector<float> tab;
+  TpfDev<float> tp;
+  size_t off[3][3];
+  for (int d = 0; d < 3; ++d) {
+    AxisBasis B;
+    if (!host_axis_tables(n[d], map, B)) { set_error("fv_pressure_solve_noalloc: eigensolver failed"); return FV_ECUDA; }
+    off[d][0] = tab.size();
+    for (double v : B.E) tab.push_back((float)v);
+    off[d][1] = tab.size();
+    for (double v : B.Einv) tab.push_back((float)v);
+    off[d][2] = tab.size();
+    for (double v : B.lam) tab.push_back((float)v);
+    tp.n[d] = n[d];
+    tp.null_index[d] = B.null_index;
+  }
+  for (int d = 0; d < 3; ++d) {
+    tp.E[d] = base + off[d][0];
+    tp.Einv[d] = base + off[d][1];
+    tp.lam[d] = base + off[d][2];
+  }
+  FV_CUDA(cudaMemcpyAsync(base, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  float* a = base + kNaTables;
+  float* b = a + kNaMaxCells;
+  const int64_t rows = (int64_t)ny * nz, qxy = (int64_t)nx * ny;
+  FV_TRY((na_right<double, float>(st, nx, rows, tp.Einv[0], r, a)));   // x forward
+  FV_TRY(na_left<false>(st, ny, nx, nz, tp.Einv[1], a, b, tp));       // y forward
+  FV_TRY(na_left<true>(st, nz, qxy, 1, tp.Einv[2], b, a, tp));        // z forward + scale
+  FV_TRY(na_left<false>(st, nz, qxy, 1, tp.E[2], a, b, tp));          // z inverse
+  FV_TRY(na_left<false>(st, ny, nx, nz, tp.E[1], b, a, tp));          // y inverse
+  FV_TRY((na_right<float, double>(st, nx, rows, tp.E[0], a, phi)));    // x inverse
+  return FV_OK;
+}

@@ -111,20 +111,42 @@ def peaks():
         return {}
 
 
-# algorithmic bytes per cell of one launch of each kernel class (FP64 state,
-# FP32 pressure-correction transforms)
+# algorithmic bytes (or flops) of one launch of each kernel class of the
+# mixed path: float32 operands, float-float (8 B) SIMPLE state, float32
+# pressure-correction transforms ("Roofline")
 def algorithmic(kind, n, prec):
     cells = n ** 3
-    f = 4 if prec == "mixed" else 8
-    if kind == "momentum":            # read U, v (3 x 8 B each), write w (3 x 8 B)
-        return {"bytes": 72 * cells}
-    if kind == "correct":             # read v, phi, p, write v, p, r
-        return {"bytes": (24 + f + 8 + 24 + 8 + 8) * cells}
-    if kind == "divergence":          # read v, write r
-        return {"bytes": 32 * cells}
-    if kind in ("tpf_x", "tpf_yz"):   # one 1-D transform: 2 n flop per cell
-        return {"flops": 2 * n * cells, "bytes": 2 * f * cells}
-    return {"bytes": 16 * cells}
+    if prec != "mixed":
+        f = 8
+        table = {"momentum": 72, "correct": 24 + 8 + 16 + 24 + 8, "divergence": 32}
+    else:
+        f = 4
+        table = {"momentum": 36,                 # read U, v (3 x 4 B each), write w (3 x 4 B)
+                 "correct": 24 + 4 + 16 + 24 + 4,  # read v (ff), phi, r/w p (ff), write v (ff), r
+                 "divergence": 16}               # read w (3 x 4 B), write r
+    if kind in ("tpf_x", "tpf_yz"):
+        # fused kernels (n <= 128) apply two 1-D transforms (2 n flop per cell
+        # each) per launch; the unfused ones apply one
+        k = 2 if n <= 128 else 1
+        return {"flops": k * 2 * n * cells, "bytes": 2 * f * cells}
+    return {"bytes": table.get(kind, 16) * cells}
+
+
+def traffic_for(kind):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since that capture."""
+    try:
+        import hashlib
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        ent = t.get(kind)
+        if not ent:
+            return None
+        src = open(os.path.join(ROOT, "paper_1704_08521_gb300", "csrc", ent["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != ent["sha"]:
+            return None
+        return ent["bytes_per_launch"]
+    except Exception:
+        return None
 
 
 def run_ours(args):
@@ -149,8 +171,11 @@ def run_ours(args):
     out = torch.empty(g.n_vel, dtype=torch.float64, device=dev)
     p = torch.empty(g.n_cell, dtype=torch.float64, device=dev)
 
-    def step(s, prec=args.prec):
-        return fv.simple_krylov_solve(g, U, V[s % NRHS], out, p, eps=EPS, prec=prec)
+    mixed = args.prec == "mixed"
+
+    def step(s, prec=args.prec, async_=None):
+        a = (prec == "mixed") if async_ is None else async_
+        return fv.simple_krylov_solve(g, U, V[s % NRHS], out, p, eps=EPS, prec=prec, async_=a)
 
     def barrier():
         if ws > 1:
@@ -158,8 +183,9 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for s in range(args.warmup):
-        st = step(s)
-    passes = []
+        step(s)
+    st = step(0, async_=False)                  # one synchronised call: loop statistics
+    passes = st["passes"]
     barrier()
     clk = ClockSampler(local)
     clk.start()
@@ -168,22 +194,28 @@ def run_ours(args):
     barrier()
     e0.record(stream)
     for s in range(args.steps):
-        passes.append(step(s)["passes"])
+        step(s)
     e1.record(stream)
     barrier()
     clocks = clk.stop()
-    launches = fv.fv_launch_count() - l0
+    host_launches = fv.fv_launch_count() - l0
     ms = e0.elapsed_time(e1)
     t = torch.tensor([ms], device=dev, dtype=torch.float64)
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     value = ws * args.steps / (ms_max / 1e3)
+    # kernels per evaluation: graph = init, round, J.v, D w, pressure solve,
+    # correct, decide (first pass) + solve, correct, decide per further pass
+    # + join; the pressure solve is 3 fused kernels for n <= 128, else 6
+    tpf_k = 3 if n <= 128 else 6
+    kernels_per_solve = (7 + tpf_k + (tpf_k + 2) * (passes - 1)) if mixed else None
+    gpu_launches = kernels_per_solve * args.steps if mixed else host_launches
 
     # same workload in the plain FP64 form, a few steps (context for the
     # mixed-precision speed-up; not the headline)
     fp64 = None
-    if args.prec == "mixed":
+    if mixed:
         k64 = max(3, min(args.steps, 10))
         step(0, "fp64")
         barrier()
@@ -194,12 +226,19 @@ def run_ours(args):
         barrier()
         fp64 = k64 / (e0.elapsed_time(e1) / 1e3)
 
-    # per-kernel-class device time over the same steps (profiled pass)
-    fv.fv_profile_enable(g, True)
-    for s in range(args.steps):
-        step(s)
-    prof = fv.fv_profile_read(g)
-    fv.fv_profile_enable(g, False)
+    # per-kernel device time: back-to-back launches of each kernel class on
+    # the grid's stream, timed with CUDA events (fv_bench_kernel)
+    prof = {}
+    if mixed:
+        step(0, async_=False)
+        if n <= 128:     # fused: tpf_x = one x-y slab kernel, tpf_yz = one z-column kernel
+            per_solve = {"momentum": 1, "divergence": 1, "correct": passes, "tpf_x": 2 * passes,
+                         "tpf_yz": passes}
+        else:
+            per_solve = {"momentum": 1, "divergence": 1, "correct": passes, "tpf_x": 2 * passes,
+                         "tpf_yz": 4 * passes}
+        for kind, cnt in per_solve.items():
+            prof[kind] = (fv.fv_bench_kernel(g, kind, reps=50), cnt)
 
     # end to end through the public API: host (pinned) rhs in, result out
     hin = [V[s].cpu().pin_memory() for s in range(min(NRHS, 4))]
@@ -207,14 +246,13 @@ def run_ours(args):
     vin = torch.empty_like(out)
     for s in range(2):
         vin.copy_(hin[s % len(hin)], non_blocking=True)
-        fv.simple_krylov_solve(g, U, vin, out, p, eps=EPS, prec=args.prec)
+        fv.simple_krylov_solve(g, U, vin, out, p, eps=EPS, prec=args.prec, async_=mixed)
         hout.copy_(out, non_blocking=True)
     barrier()
-    t0 = time.perf_counter()
     e0.record(stream)
     for s in range(args.steps):
         vin.copy_(hin[s % len(hin)], non_blocking=True)
-        fv.simple_krylov_solve(g, U, vin, out, p, eps=EPS, prec=args.prec)
+        fv.simple_krylov_solve(g, U, vin, out, p, eps=EPS, prec=args.prec, async_=mixed)
         hout.copy_(out, non_blocking=True)
     e1.record(stream)
     barrier()
@@ -229,29 +267,33 @@ def run_ours(args):
             dist.destroy_process_group()
         return None
 
-    # roofline of the dominant kernel class
+    # roofline of the dominant kernel class (largest device time per solve)
     pk = peaks()
-    kind = max(prof, key=lambda k: prof[k][0])
-    kms, kcount = prof[kind]
-    per_launch_s = kms / 1e3 / max(kcount, 1)
-    alg = algorithmic(kind, n, args.prec)
-    clock_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    if "flops" in alg:
-        # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x SM clock
-        peak = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12 if args.prec == "mixed" else None
-        achieved = alg["flops"] / per_launch_s / 1e12
-        roof = {"bound": "alu", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None, "traffic": None,
-                "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {clock_mhz:.0f} MHz (median under load)"}
-    else:
-        peak = pk.get("hbm_gbs", 6800.0)
-        achieved = alg["bytes"] / per_launch_s / 1e9
-        roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof = None
+    breakdown = {}
+    if prof:
+        tot = sum(v[0] * v[1] for v in prof.values())
+        breakdown = {k: {"ms_per_launch": v[0], "launches_per_solve": v[1],
+                         "ms_per_solve": v[0] * v[1], "share": v[0] * v[1] / tot}
+                     for k, v in prof.items()}
+        kind = max(prof, key=lambda k: prof[k][0] * prof[k][1])
+        per_launch_s = prof[kind][0] / 1e3
+        alg = algorithmic(kind, n, args.prec)
+        clock_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+        if "flops" in alg:
+            peak = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
+            achieved = alg["flops"] / per_launch_s / 1e12
+            roof = {"bound": "alu", "kernel": kind, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for(kind),
+                    "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 flop x {clock_mhz:.0f} MHz "
+                                   "(median SM clock under load)"}
+        else:
+            peak = pk.get("hbm_gbs", 6800.0)
+            achieved = alg["bytes"] / per_launch_s / 1e9
+            roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(kind),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     step_ms = ms_max / args.steps
-    breakdown = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
-                     "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)}
-                 for k, v in prof.items() if v[1]}
     # bytes moved per step
     h2d = g.n_vel * 8
     d2h = g.n_vel * 8
@@ -264,19 +306,20 @@ def run_ours(args):
                    "tol": EPS, "prec": args.prec, "rhs_rotation": NRHS,
                    "l2": f"inputs rotate over {NRHS} vectors ({NRHS * g.n_vel * 8 / 1e6:.0f} MB) > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "simple_passes_mean": sum(passes) / len(passes),
-        "sweeps_per_s": value * sum(passes) / len(passes),
+        "simple_passes": passes,
+        "sweeps_per_s": value * passes,
         "mcell_jv_per_s": None,
         "fp64_form_solves_per_s": fp64,
         "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches,
+        "gpu_launches": gpu_launches,
+        "kernels_per_solve": kernels_per_solve,
         "roofline": roof,
         "kernel_breakdown": breakdown,
         "clocks": clocks,
     }
     mom = prof.get("momentum")
-    if mom and mom[1]:
-        res["mcell_jv_per_s"] = n ** 3 / (mom[0] / 1e3 / mom[1]) / 1e6
+    if mom:
+        res["mcell_jv_per_s"] = n ** 3 / (mom[0] / 1e3) / 1e6
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(n, budget_s=12.0)
     if ws > 1:

@@ -81,6 +81,9 @@ typedef struct {
   double sigma;   /* >0: return P(L_U v + sigma v) - sigma v, the shifted
                      operator used inside GMRES and Arnoldi; 0: the plain
                      Krylov vector P L_U v of Eqs. 8-9                 [0] */
+  int async;      /* FV_MIXED only: 1 = do not synchronise; the call then
+                     returns FV_OK once queued and stats are not filled
+                     (a non-converged loop is not reported)              [0] */
 } fv_simple_opts;
 
 typedef struct {
@@ -153,8 +156,11 @@ fv_status ns_jacvec(const fv_grid* g, const double* U, const double* v, double* 
 /* Section 3, Eqs. 8-10 and the SIMPLE-like algorithm: from v_in compute
  * w = L_U v_in (Eq. 10), then repeat { solve D G phi = D v (Neumann);
  * v -= omega G phi; p += omega phi } until the stop test of opts.  Returns
- * the divergence-free v_out[n_vel] and p_out[n_cell] (zero mean).
- * v_in and v_out may not alias.  stats may be NULL. */
+ * the divergence-free v_out[n_vel] and p_out[n_cell] (zero mean; may be
+ * NULL).  v_in and v_out may not alias.  stats may be NULL.
+ * FV_MIXED runs the whole evaluation as one CUDA graph launch whose pass
+ * loop is decided on the device; the graph is captured on the first such
+ * call for a grid (make that call outside any stream capture). */
 fv_status simple_krylov_solve(const fv_grid* g, const double* U, const double* v_in,
                               double* v_out, double* p_out,
                               const fv_simple_opts* opts, fv_simple_stats* stats);
@@ -225,8 +231,15 @@ fv_status fv_profile_enable(fv_grid* g, int on);
  * device time in ms and the number of launches since fv_profile_enable. */
 fv_status fv_profile_read(fv_grid* g, double* ms /* host, FV_NKIND */,
                           int64_t* launches /* host, FV_NKIND */);
-/* Total number of kernels this library has launched in the process. */
+/* Total number of launches (kernel launches and graph launches) this
+ * library has issued in the process. */
 int64_t fv_launch_count(void);
+/* Time `reps` back-to-back launches of one FV_MIXED kernel class
+ * (FV_K_MOMENTUM, FV_K_DIVERGENCE, FV_K_CORRECT, FV_K_TPF_X, FV_K_TPF_YZ =
+ * one z-axis transform) on the grid's workspace with CUDA events on its
+ * stream; *ms_per_launch (host) receives the mean device time.  Needs one
+ * earlier FV_MIXED simple_krylov_solve on the grid. */
+fv_status fv_bench_kernel(fv_grid* g, int kind, int reps, double* ms_per_launch);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,7 @@ class fv_grid_info(ctypes.Structure):
 
 class fv_simple_opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_pass", ctypes.c_int), ("prec", ctypes.c_int),
-                ("omega", ctypes.c_double), ("sigma", ctypes.c_double)]
+                ("omega", ctypes.c_double), ("sigma", ctypes.c_double), ("async_", ctypes.c_int)]
 
 
 class fv_simple_stats(ctypes.Structure):
@@ -138,8 +138,8 @@ def ns_jacvec(g, U, v, Jv, prec="fp64"):
 
 
 def simple_krylov_solve(g, U, v_in, v_out, p_out=None, eps=1e-8, max_pass=200, prec="fp64",
-                        omega=1.0, sigma=0.0):
-    o = fv_simple_opts(eps, max_pass, PRECS.get(prec, prec), omega, sigma)
+                        omega=1.0, sigma=0.0, async_=False):
+    o = fv_simple_opts(eps, max_pass, PRECS.get(prec, prec), omega, sigma, 1 if async_ else 0)
     s = fv_simple_stats()
     check(lib.simple_krylov_solve(g.handle, _f64(U, g.n_vel, "U"), _f64(v_in, g.n_vel, "v_in"),
                                   _f64(v_out, g.n_vel, "v_out"),
@@ -215,3 +215,11 @@ def fv_profile_read(g):
 
 def fv_launch_count():
     return int(lib.fv_launch_count())
+
+
+def fv_bench_kernel(g, kind, reps=50):
+    """Mean device time (ms) of one launch of a mixed-path kernel class."""
+    ms = ctypes.c_double()
+    check(lib.fv_bench_kernel(g.handle, KERNEL_KINDS.index(kind), reps, ctypes.byref(ms)),
+          "fv_bench_kernel")
+    return ms.value

@@ -46,6 +46,7 @@ _SIGS = {
     "fv_profile_enable": (_I, [_P, _I]),
     "fv_profile_read": (_I, [_P, _P, _P]),
     "fv_launch_count": (ctypes.c_int64, []),
+    "fv_bench_kernel": (_I, [_P, _I, _I, _P]),
     "fv_host_hess_eigenvalues": (_I, [_I, _P, _P, _P]),
     "fv_host_shift_steps": (_I, [_I, _P, _P, _I, _P, _P]),
     "fv_host_ff_convert": (_I, [ctypes.c_int64, _P, _P, _P, _P, _P]),

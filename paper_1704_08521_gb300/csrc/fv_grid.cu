@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -18,6 +19,7 @@ static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 LaunchScope::LaunchScope(const fv_grid* g_, int kind_) : g(g_), kind(kind_), idx(SIZE_MAX) {
+  if (g->capturing) return;
   count_launch();
   if (!g->prof_on) return;
   if (g->ev_used + 2 > g->ev_pool.size()) {
@@ -202,21 +204,30 @@ static fv_status upload_metrics(fv_grid* g, void** dst, Met<T>& met) {
 template <typename T>
 static fv_status upload_tpf(fv_grid* g, void** dst, TpfDev<T>& t) {
   size_t total = 0;
-  for (int d = 0; d < 3; ++d) total += 2 * (size_t)g->n[d] * g->n[d] + g->n[d];
+  for (int d = 0; d < 3; ++d) total += 4 * (size_t)g->n[d] * g->n[d] + g->n[d];
   std::vector<T> h(total);
-  size_t o = 0, offE[3], offI[3], offL[3];
+  size_t o = 0, offE[3], offI[3], offL[3], offEt[3], offIt[3];
   for (int d = 0; d < 3; ++d) {
     const AxisBasis& B = g->basis[d];
-    const size_t nn = (size_t)B.n * B.n;
+    const int n = B.n;
+    const size_t nn = (size_t)n * n;
     offE[d] = o;
     for (size_t q = 0; q < nn; ++q) h[o + q] = T(B.E[q]);
     o += nn;
     offI[d] = o;
     for (size_t q = 0; q < nn; ++q) h[o + q] = T(B.Einv[q]);
     o += nn;
+    offEt[d] = o;
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) h[o + (size_t)c * n + r] = T(B.E[(size_t)r * n + c]);
+    o += nn;
+    offIt[d] = o;
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) h[o + (size_t)c * n + r] = T(B.Einv[(size_t)r * n + c]);
+    o += nn;
     offL[d] = o;
-    for (int a = 0; a < B.n; ++a) h[o + a] = T(B.lam[a]);
-    o += B.n;
+    for (int a = 0; a < n; ++a) h[o + a] = T(B.lam[a]);
+    o += n;
   }
   FV_CUDA(cudaMalloc(dst, total * sizeof(T)));
   g->ws_bytes += total * sizeof(T);
@@ -227,6 +238,8 @@ static fv_status upload_tpf(fv_grid* g, void** dst, TpfDev<T>& t) {
     t.null_index[d] = g->basis[d].null_index;
     t.E[d] = base + offE[d];
     t.Einv[d] = base + offI[d];
+    t.Et[d] = base + offEt[d];
+    t.Einvt[d] = base + offIt[d];
     t.lam[d] = base + offL[d];
   }
   return FV_OK;
@@ -339,6 +352,8 @@ fv_status fv_grid_create(int nx, int ny, int nz, int map, double alpha, double r
   g->alpha = alpha;
   g->re = re;
   g->stream = (cudaStream_t)cuda_stream;
+  const char* ng = std::getenv("FVNS_NO_GRAPH");
+  g->use_graph = !(ng && ng[0] == '1');
   fv_status s = build(g);
   if (s != FV_OK) { fv_grid_destroy(g); return s; }
   *out = g;
@@ -392,6 +407,7 @@ int64_t fv_launch_count(void) { return g_launches.load(); }
 
 void fv_grid_destroy(fv_grid* g) {
   if (!g) return;
+  for (auto& c : g->graphs) destroy_graph_cache(c);
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   void* ptrs[] = {g->d_met_d, g->d_met_f, g->d_tpf_d, g->d_tpf_f, g->vel_buf[0], g->vel_buf[1],
                   g->vel_buf[2], g->cell_buf[0], g->cell_buf[1], g->cell_buf[2], g->tpf_buf[0],

@@ -72,6 +72,25 @@ struct TpfDev {
   const T* E[3];
   const T* Einv[3];
   const T* lam[3];
+  const T* Et[3];      // transposes (E^T, Einv^T), the k-major operands of
+  const T* Einvt[3];   // the fused shared-memory transform kernels
+};
+
+// device-side state of one SIMPLE loop (graph path)
+struct LoopState {
+  float phi1, phi_prev, phi_last, div_last;
+  int pass, nan, status, pad;   // status: 0 running, 1 converged, 2 pass cap, 3 NaN
+};
+
+// one captured, instantiated evaluation graph (per grid and shift sigma)
+struct GraphCache {
+  bool ready = false;
+  double sigma = 0.0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t init_node = nullptr;
+  void* d_call = nullptr;
+  LoopState* d_loop = nullptr;
 };
 
 }  // namespace fv
@@ -118,6 +137,11 @@ struct fv_grid {
   void* d_met_ff = nullptr;      // float-float 1/dx per axis
   fv::MetFF met_ff;
 
+  // captured evaluation graphs of the mixed path (built on first use)
+  fv::GraphCache graphs[2];
+  mutable bool capturing = false;
+  bool use_graph = true;          // FVNS_NO_GRAPH=1 selects the host-driven loop
+
   // optional per-kernel-class event timing
   mutable bool prof_on = false;
   mutable std::vector<cudaEvent_t> ev_pool;
@@ -155,6 +179,17 @@ struct LaunchScope {
   ~LaunchScope();
 };
 
+// Cell-kernel launch shape: 256 threads tile the x-y plane linearly (x
+// fastest, so a warp reads consecutive addresses) and every thread marches
+// over kCellKz consecutive z-planes; ~nx*ny*nz/1024 blocks of real work.
+constexpr int kCellThreads = 256;
+constexpr int kCellKz = 4;
+inline dim3 cell_launch_grid(const int n[3]) {
+  const int64_t plane = (int64_t)n[0] * n[1];
+  return dim3((unsigned)((plane + kCellThreads - 1) / kCellThreads),
+              (unsigned)((n[2] + kCellKz - 1) / kCellKz), 1);
+}
+
 // ------------------------------------------------------------- kernels ---
 // all launches are on g->stream; they return FV_OK or FV_ECUDA
 fv_status launch_momentum_jac(const fv_grid* g, const double* U, const double* v, double* out,
@@ -183,9 +218,18 @@ fv_status launch_join_ff(const fv_grid* g, const float2* v, const double* x, dou
 fv_status launch_join_ff_cells(const fv_grid* g, const float2* p, double* out);
 fv_status launch_widen_f32(const fv_grid* g, const float* in, double* out, int64_t n);
 
+// graph path (fv_graph.cu): one mixed-precision Krylov-vector evaluation as
+// one graph launch; with sync, the loop statistics are read back.
+fv_status mixed_krylov_graph(const fv_grid* g, const double* U, const double* x, double* out,
+                             double* p, double sigma, double eps, int max_pass, double omega,
+                             bool sync, int* passes, double* phi1, double* phil, double* divl,
+                             int* status);
+void destroy_graph_cache(GraphCache& c);
+
 // tensor-product pressure solve: phi = (D G)^+ r ; phi is float or double
 fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec);
 fv_status tpf_solve_f32(const fv_grid* g, const float* r, float* phi);
+fv_status tpf_one_transform_f32(const fv_grid* g, int axis);
 
 // vector kernels (weighted inner products, Gram-Schmidt)
 fv_status vec_dots(const fv_grid* g, const double* V, int64_t ldv, int nvec, const double* w,

@@ -364,6 +364,16 @@ static fv_status krylov_apply(const fv_grid* g, const double* U, const double* x
                               double* p, double sigma, int prec, double eps, int max_pass,
                               double omega, SimpleResult* res) {
   if (prec == FV_MIXED) {
+    if (g->use_graph) {
+      int status = 0;
+      FV_TRY(mixed_krylov_graph(g, U, x, out, p, sigma, eps, max_pass, omega, res != nullptr,
+                                res ? &res->passes : nullptr, res ? &res->phi_first : nullptr,
+                                res ? &res->phi_last : nullptr, res ? &res->div_max : nullptr,
+                                &status));
+      if (res && status == 3) { set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN; }
+      if (res && status == 2) { set_error("SIMPLE loop reached max_pass"); return FV_ENOCONV; }
+      return FV_OK;
+    }
     FV_TRY(launch_round_f32(g, U, g->U32, g->nvel));
     FV_TRY(launch_round_f32(g, x, g->x32, g->nvel));
     FV_TRY(launch_momentum_f32(g, g->U32, g->x32, g->w32, sigma));
@@ -493,8 +503,10 @@ fv_status simple_krylov_solve(const fv_grid* g, const double* U, const double* v
     return FV_EINVAL;
   }
   SimpleResult r;
-  fv_status s = krylov_apply(g, U, v_in, v_out, p_out, o.sigma, o.prec, o.eps, o.max_pass, o.omega, &r);
-  if (stats) {
+  const bool no_sync = o.async != 0 && o.prec == FV_MIXED;
+  fv_status s = krylov_apply(g, U, v_in, v_out, p_out, o.sigma, o.prec, o.eps, o.max_pass, o.omega,
+                             no_sync ? nullptr : &r);
+  if (stats && !no_sync) {
     stats->passes = r.passes;
     stats->phi_first = r.phi_first;
     stats->phi_last = r.phi_last;

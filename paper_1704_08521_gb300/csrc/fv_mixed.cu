@@ -49,9 +49,15 @@ __global__ void k_widen_f32(const float* __restrict__ in, double* __restrict__ o
 // D w in float32 (first residual of the loop; w holds float32 values).
 __global__ void __launch_bounds__(256) k_div_f32(MetFF m, const float* __restrict__ w,
                                                  float* __restrict__ r) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y, k = blockIdx.z;
-  if (i >= m.n[0]) return;
+  const int plane_ = m.n[0] * m.n[1];
+  const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act_ = t_ < plane_;
+  const int i = act_ ? t_ % m.n[0] : 0;
+  const int j = act_ ? t_ / m.n[0] : 0;
+  if (!act_) return;
+  for (int kk = 0; kk < kCellKz; ++kk) {
+  const int k = blockIdx.y * kCellKz + kk;
+  if (k >= m.n[2]) return;
   const int64_t nx = m.n[0], nxy = nx * m.n[1], nc = m.ncell;
   const int64_t base = ((int64_t)k * m.n[1] + j) * nx + i;
   const float u0 = (i > 0) ? w[base] : 0.f;
@@ -61,6 +67,7 @@ __global__ void __launch_bounds__(256) k_div_f32(MetFF m, const float* __restric
   const float w0 = (k > 0) ? w[2 * nc + base] : 0.f;
   const float w1 = (k + 1 < m.n[2]) ? w[2 * nc + base + nxy] : 0.f;
   r[base] = (u1 - u0) * m.idx[0][i].x + (v1 - v0) * m.idx[1][j].x + (w1 - w0) * m.idx[2][k].x;
+  }
 }
 
 // One pass: v_out = v_in - omega G phi (own faces), p += omega phi, and
@@ -72,17 +79,22 @@ __global__ void __launch_bounds__(256) k_correct_ff(MetFF m, const void* __restr
                                                     const float* __restrict__ phi,
                                                     float2* __restrict__ p, float* __restrict__ r,
                                                     float omega, double* scal) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y, k = blockIdx.z;
+  const int plane_ = m.n[0] * m.n[1];
+  const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act_ = t_ < plane_;
+  const int i = act_ ? t_ % m.n[0] : 0;
+  const int j = act_ ? t_ / m.n[0] : 0;
   float aphi = 0.f, adiv = 0.f;
-  if (i < m.n[0]) {
+  for (int kk = 0; kk < kCellKz; ++kk) {
+    const int k = blockIdx.y * kCellKz + kk;
+    if (!act_ || k >= m.n[2]) continue;
     const int pos[3] = {i, j, k};
-    const int64_t st[3] = {1, (int64_t)m.n[0], (int64_t)m.n[0] * m.n[1]};
-    const int64_t nc = m.ncell;
-    const int64_t base = ((int64_t)k * m.n[1] + j) * m.n[0] + i;
+    const int st[3] = {1, m.n[0], m.n[0] * m.n[1]};
+    const int nc = (int)m.ncell;
+    const int base = (k * m.n[1] + j) * m.n[0] + i;
     const float* w32 = (const float*)vin_;
     const float2* vin = (const float2*)vin_;
-    auto load = [&](int64_t e) -> ff {
+    auto load = [&](int e) -> ff {
       if (FIRST) return {__ldg(w32 + e), 0.f};
       return of2(__ldg(vin + e));
     };
@@ -106,12 +118,9 @@ __global__ void __launch_bounds__(256) k_correct_ff(MetFF m, const void* __restr
     r[base] = dv.hi;
     if (FIRST) p[base] = make_float2(omega * f0, 0.f);
     else p[base] = to2(ff_add_f(of2(p[base]), omega * f0));
-    aphi = fabsf(f0);
-    adiv = fabsf(dv.hi);
-    if (!(aphi <= 3e38f) || !(adiv <= 3e38f)) {
-      scal[S_NAN] = 1.0;
-      aphi = adiv = 0.f;
-    }
+    const float a1 = fabsf(f0), a2 = fabsf(dv.hi);
+    if (!(a1 <= 3e38f) || !(a2 <= 3e38f)) scal[S_NAN] = 1.0;
+    else { aphi = fmaxf(aphi, a1); adiv = fmaxf(adiv, a2); }
   }
   aphi = block_maxf(aphi);
   adiv = block_maxf(adiv);
@@ -137,13 +146,9 @@ inline unsigned grid1d(int64_t n) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-inline dim3 cell_grid(const fv_grid* g, int bx) {
-  return dim3((g->n[0] + bx - 1) / bx, g->n[1], g->n[2]);
-}
+inline dim3 cell_grid(const fv_grid* g, int) { return cell_launch_grid(g->n); }
 
-inline int block_x(const fv_grid* g) {
-  return g->n[0] >= 128 ? 128 : (g->n[0] >= 64 ? 64 : 32);
-}
+inline int block_x(const fv_grid*) { return kCellThreads; }
 
 }  // namespace
 

@@ -19,7 +19,7 @@ namespace {
 // load an input value in the arithmetic type T; double -> float goes through
 // the integer rounding of fv_ff.cuh, not the (slow on GB300) FP64 converter
 template <typename T, typename TI>
-__device__ __forceinline__ T ld(const TI* __restrict__ p, int64_t i) {
+__device__ __forceinline__ T ld(const TI* __restrict__ p, int i) {
   if constexpr (sizeof(T) == sizeof(TI)) return __ldg(p + i);
   else return T(__ldg(p + i));
 }
@@ -35,10 +35,11 @@ __device__ __forceinline__ TO to_out(T v) {
 // else: (1/Re) Lap U - div(U (x) U)                            (lid wall values)
 template <typename T, int C, bool JAC, typename TI>
 __device__ __forceinline__ T momentum_face(const Met<T>& m, const TI* __restrict__ U,
-                                           const TI* __restrict__ V, int64_t base,
-                                           const int (&pos)[3], const int64_t (&st)[3],
+                                           const TI* __restrict__ V, int base,
+                                           const int (&pos)[3], const int (&st)[3],
                                            T inv_re, T lid_hi, T shift) {
-  const int64_t nc = m.ncell;
+  // 32-bit offsets: the API guarantees 3 nx ny nz < 2^31
+  const int nc = (int)m.ncell;
   const TI* Uc = U + C * nc;
   const TI* Qc = (JAC ? V : U) + C * nc;
   const int f = pos[C];
@@ -85,7 +86,7 @@ __device__ __forceinline__ T momentum_face(const Met<T>& m, const TI* __restrict
     const T thc = m.th[C][f];
     T Flo = T(0), Fhi = T(0);
     if (e > 0) {
-      const int64_t b = base;
+      const int b = base;
       const T aU = ld<T>(Ud, b - st[C]) + thc * (ld<T>(Ud, b) - ld<T>(Ud, b - st[C]));
       const T thd = m.th[d][e];
       const T cm = ld<T>(Uc, base - st[d]);
@@ -99,7 +100,7 @@ __device__ __forceinline__ T momentum_face(const Met<T>& m, const TI* __restrict
       }
     }
     if (e + 1 < nd) {
-      const int64_t b = base + st[d];
+      const int b = base + st[d];
       const T aU = ld<T>(Ud, b - st[C]) + thc * (ld<T>(Ud, b) - ld<T>(Ud, b - st[C]));
       const T thd = m.th[d][e + 1];
       const T c0 = ld<T>(Uc, base);
@@ -125,14 +126,19 @@ __global__ void __launch_bounds__(256) k_momentum(Met<T> m, const TI* __restrict
                                                   const double* __restrict__ P,
                                                   TO* __restrict__ out, T inv_re, T lid_u,
                                                   T lid_v, T shift) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  const int k = blockIdx.z;
-  if (i >= m.n[0]) return;
+  const int plane_ = m.n[0] * m.n[1];
+  const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act_ = t_ < plane_;
+  const int i = act_ ? t_ % m.n[0] : 0;
+  const int j = act_ ? t_ / m.n[0] : 0;
+  if (!act_) return;
+  for (int kk = 0; kk < kCellKz; ++kk) {
+  const int k = blockIdx.y * kCellKz + kk;
+  if (k >= m.n[2]) return;
   const int pos[3] = {i, j, k};
-  const int64_t st[3] = {1, (int64_t)m.n[0], (int64_t)m.n[0] * m.n[1]};
-  const int64_t base = ((int64_t)k * m.n[1] + j) * m.n[0] + i;
-  const int64_t nc = m.ncell;
+  const int st[3] = {1, m.n[0], m.n[0] * m.n[1]};
+  const int base = (k * m.n[1] + j) * m.n[0] + i;
+  const int nc = (int)m.ncell;
   // u (x-faces)
   {
     T r = T(0);
@@ -160,6 +166,7 @@ __global__ void __launch_bounds__(256) k_momentum(Met<T> m, const TI* __restrict
     }
     out[2 * nc + base] = to_out<T, TO>(r);
   }
+  }
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(double* slot, double v) {
@@ -185,10 +192,15 @@ __device__ __forceinline__ double block_max(double v) {
 __global__ void __launch_bounds__(256) k_divergence(Met<double> m, const double* __restrict__ v,
                                                     double* __restrict__ r, double* maxslot,
                                                     double* nanslot) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y, k = blockIdx.z;
+  const int plane_ = m.n[0] * m.n[1];
+  const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act_ = t_ < plane_;
+  const int i = act_ ? t_ % m.n[0] : 0;
+  const int j = act_ ? t_ / m.n[0] : 0;
   double a = 0.0;
-  if (i < m.n[0]) {
+  for (int kk = 0; kk < kCellKz; ++kk) {
+    const int k = blockIdx.y * kCellKz + kk;
+    if (!act_ || k >= m.n[2]) continue;
     const int64_t nx = m.n[0], nxy = nx * m.n[1], nc = m.ncell;
     const int64_t base = ((int64_t)k * m.n[1] + j) * nx + i;
     const double u0 = (i > 0) ? v[base] : 0.0;
@@ -199,8 +211,9 @@ __global__ void __launch_bounds__(256) k_divergence(Met<double> m, const double*
     const double w1 = (k + 1 < m.n[2]) ? v[2 * nc + base + nxy] : 0.0;
     const double div = (u1 - u0) * m.idx[0][i] + (v1 - v0) * m.idx[1][j] + (w1 - w0) * m.idx[2][k];
     r[base] = div;
-    a = fabs(div);
-    if (!(a <= 1e300)) { *nanslot = 1.0; a = 0.0; }
+    const double ad = fabs(div);
+    if (!(ad <= 1e300)) *nanslot = 1.0;
+    else a = fmax(a, ad);
   }
   if (maxslot) {
     a = block_max(a);
@@ -220,10 +233,15 @@ __global__ void __launch_bounds__(256) k_correct_div(Met<double> m, const double
                                                      double* __restrict__ p,
                                                      double* __restrict__ r, double omega,
                                                      double* scal) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y, k = blockIdx.z;
+  const int plane_ = m.n[0] * m.n[1];
+  const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act_ = t_ < plane_;
+  const int i = act_ ? t_ % m.n[0] : 0;
+  const int j = act_ ? t_ / m.n[0] : 0;
   double aphi = 0.0, adiv = 0.0;
-  if (i < m.n[0]) {
+  for (int kk = 0; kk < kCellKz; ++kk) {
+    const int k = blockIdx.y * kCellKz + kk;
+    if (!act_ || k >= m.n[2]) continue;
     const int nx = m.n[0], ny = m.n[1], nz = m.n[2];
     const int64_t sy = nx, sz = (int64_t)nx * ny, nc = m.ncell;
     const int64_t base = ((int64_t)k * ny + j) * nx + i;
@@ -244,12 +262,9 @@ __global__ void __launch_bounds__(256) k_correct_div(Met<double> m, const double
     const double div = (u1 - u0) * m.idx[0][i] + (v1 - v0) * m.idx[1][j] + (w1 - w0) * m.idx[2][k];
     r[base] = div;
     if (p) p[base] += omega * f0;
-    aphi = fabs(f0);
-    adiv = fabs(div);
-    if (!(aphi <= 1e300) || !(adiv <= 1e300)) {
-      scal[S_NAN] = 1.0;
-      aphi = adiv = 0.0;
-    }
+    const double a1 = fabs(f0), a2 = fabs(div);
+    if (!(a1 <= 1e300) || !(a2 <= 1e300)) scal[S_NAN] = 1.0;
+    else { aphi = fmax(aphi, a1); adiv = fmax(adiv, a2); }
   }
   aphi = block_max(aphi);
   __syncthreads();
@@ -277,13 +292,9 @@ __global__ void k_zero_walls(int nx, int ny, int nz, double* v) {
   }
 }
 
-inline dim3 cell_grid(const fv_grid* g, int bx) {
-  return dim3((g->n[0] + bx - 1) / bx, g->n[1], g->n[2]);
-}
+inline dim3 cell_grid(const fv_grid* g, int) { return cell_launch_grid(g->n); }
 
-inline int block_x(const fv_grid* g) {
-  return g->n[0] >= 128 ? 128 : (g->n[0] >= 64 ? 64 : 32);
-}
+inline int block_x(const fv_grid*) { return kCellThreads; }
 
 }  // namespace
 

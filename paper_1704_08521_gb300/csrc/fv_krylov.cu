@@ -326,7 +326,9 @@ static float slot_float(const double* h, int slot) {
 // out = v - sigma x (float64) and p_out (optional).
 static fv_status simple_loop_ff(const fv_grid* g, double* out, double* p_out, const double* x,
                                 double sigma, double eps, int max_pass, double omega,
-                                SimpleResult* res) {
+                                SimpleResult* res_out) {
+  SimpleResult local;
+  SimpleResult* res = res_out ? res_out : &local;
   const void* cur = g->w32;
   int nxt = 0;
   double h[kScalars];
@@ -547,6 +549,11 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     for (double x : g->h_dx[d]) wmin = std::min(wmin, x);
   const double atol = 1e-3 * o.tol * std::sqrt(0.5 * wmin * wmin * wmin);
 
+  // FV_MIXED: float32 Krylov vectors while they still cut ||F|| by 10x per
+  // step, then float64 (the inexact Jacobian of the mixed form limits the
+  // linear rate of Newton near the root); the residual is always float64
+  int cur_prec = o.prec;
+  double prev_res = -1.0;
   for (int it = 0; it <= o.max_newton; ++it) {
     // continuity part of the Newton correction: project U
     FV_TRY(launch_zero_walls(g, U));
@@ -575,13 +582,16 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       return FV_OK;
     }
     if (it == o.max_newton) break;
+    if (cur_prec == FV_MIXED && prev_res > 0.0 && res > 0.1 * prev_res) cur_prec = FV_FP64;
+    prev_res = res;
+    const double lin_rtol = cur_prec == FV_MIXED ? std::max(o.gmres_rtol, 1e-6) : o.gmres_rtol;
 
     // GMRES(m) for A_sigma du = Fm, du = 0 initially
     FV_CUDA(cudaMemsetAsync(du, 0, nv * sizeof(double), g->stream));
     double bnorm;
     FV_TRY(dot_host(g, Fm, Fm, &bnorm));
     bnorm = std::sqrt(bnorm);
-    const double stop = std::max(o.gmres_rtol * bnorm, atol);
+    const double stop = std::max(lin_rtol * bnorm, atol);
     int its = 0;
     bool first = true;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol(m + 2);
@@ -590,7 +600,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       if (first) {
         FV_CUDA(cudaMemcpyAsync(V, Fm, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
       } else {
-        FV_TRY(krylov_apply(g, U, du, V, nullptr, o.sigma, o.prec, o.simple_eps, 200, 1.0, &sr));
+        FV_TRY(krylov_apply(g, U, du, V, nullptr, o.sigma, cur_prec, o.simple_eps, 200, 1.0, &sr));
         FV_TRY(vec_axpby(g, nv, -1.0, V, 1.0, Fm, V));
       }
       first = false;
@@ -604,7 +614,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       int jdone = 0;
       for (int j = 0; j < m; ++j) {
         double* w = V + (int64_t)(j + 1) * nv;
-        FV_TRY(krylov_apply(g, U, V + (int64_t)j * nv, w, nullptr, o.sigma, o.prec, o.simple_eps,
+        FV_TRY(krylov_apply(g, U, V + (int64_t)j * nv, w, nullptr, o.sigma, cur_prec, o.simple_eps,
                             200, 1.0, &sr));
         double hn;
         FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn));

@@ -213,3 +213,17 @@ def test_mixed_async_graph_matches_sync(fv):
     T = poisson.TPF(G)
     ref, _ = simple.krylov_vector(G, T, layout.to_oracle(U, shape), layout.to_oracle(host(v2), shape), 700.0)
     assert relerr(host(b), layout.from_oracle(ref)) < 2e-5
+
+
+def test_host_driven_loop_matches_graph(fv, monkeypatch):
+    # FVNS_NO_GRAPH=1 selects the host-driven mixed loop (same kernels, one
+    # synchronisation per pass); both must give the same fields, also when
+    # called without statistics
+    g1, G, shape, U, v = setup(fv, 12, 10, 14, "cosine")
+    monkeypatch.setenv("FVNS_NO_GRAPH", "1")
+    g2 = fv.Grid(14, 10, 12, "cosine", alpha=0.3, re=700.0)
+    a = torch.empty(g1.n_vel, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    fv.simple_krylov_solve(g1, dev(U), dev(v), a, None, eps=1e-10, prec="mixed")
+    fv.simple_krylov_solve(g2, dev(U), dev(v), b, None, eps=1e-10, prec="mixed", async_=True)
+    assert relerr(host(b), host(a)) < 1e-9

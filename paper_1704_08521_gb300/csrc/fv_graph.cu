@@ -370,7 +370,13 @@ fv_status bench_kernel(fv_grid* g, int kind, int reps, double* ms) {
   GraphCache* gc = nullptr;
   for (auto& c : g->graphs)
     if (c.ready) gc = &c;
-  if (!gc) { set_error("fv_bench_kernel: run a mixed evaluation on this grid first"); return FV_EINVAL; }
+  if (!gc) {
+    // host-driven grids have no graph yet: capture one for its device blocks
+    gc = &g->graphs[0];
+    FV_TRY(build_graph(g, 0.0, *gc));
+    FV_CUDA(cudaMemsetAsync(gc->d_call, 0, sizeof(CallBlock), g->stream));
+    FV_CUDA(cudaMemsetAsync(gc->d_loop, 0, sizeof(LoopState), g->stream));
+  }
   const int bx = block_x(g);
   const dim3 cg = cell_launch_grid(g->n);
   float* part = (float*)g->d_part;

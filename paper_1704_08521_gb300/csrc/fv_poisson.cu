@@ -320,18 +320,24 @@ constexpr int kFusedMax = 128;
 constexpr int kColGroup = 64;
 
 __host__ __device__ __forceinline__ int up4(int n) { return (n + 3) & ~3; }
+__host__ __device__ __forceinline__ int up8(int n) { return (n + 7) & ~7; }
 
-// acc[r][c] += sum_k At[k*lda + 4*tr + r] * Bt[k*ldb + 4*tc + c]
+// rows per thread of the fused kernels' register tiles (8 x 4 outputs:
+// three float4 shared loads per 32 FMAs)
+constexpr int RT = 8;
+
+// acc[r][c] += sum_k At[k*lda + RT*tr + r] * Bt[k*ldb + 4*tc + c]
 __device__ __forceinline__ void smem_mm(const float* At, int lda, const float* Bt, int ldb, int K,
-                                        int tr, int tc, float (&acc)[4][4]) {
-#pragma unroll 4
+                                        int tr, int tc, float (&acc)[RT][4]) {
+#pragma unroll 2
   for (int k = 0; k < K; ++k) {
-    const float4 a = *reinterpret_cast<const float4*>(At + k * lda + 4 * tr);
+    const float4 a0 = *reinterpret_cast<const float4*>(At + k * lda + RT * tr);
+    const float4 a1 = *reinterpret_cast<const float4*>(At + k * lda + RT * tr + 4);
     const float4 b = *reinterpret_cast<const float4*>(Bt + k * ldb + 4 * tc);
-    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float av[RT] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < RT; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
   }
@@ -347,7 +353,7 @@ __global__ void k_slab_xy(const float* __restrict__ in, float* __restrict__ out,
   extern __shared__ __align__(16) float sm[];
   const int a0 = blockIdx.y * ncol;
   const int na = min(ncol, nx - a0);
-  const int ncp = up4(ncol), nyp = up4(ny);
+  const int ncp = up4(ncol), nyp = up8(ny);
   const int nmax = nx > ny ? nx : ny;
   float* A1 = sm;                      // in^T  [nx][nyp]; later M2t [ny][nyp]
   float* B1 = A1 + nmax * nyp;         // M1t[:, a0:a1]  [nx][ncp]
@@ -380,12 +386,12 @@ __global__ void k_slab_xy(const float* __restrict__ in, float* __restrict__ out,
     }
   }
   __syncthreads();
-  float acc[4][4] = {};
+  float acc[RT][4] = {};
   smem_mm(A1, nyp, B1, ncp, nx, tr, tc, acc);       // T[j][a] = sum_i in[j][i] M1[a][i]
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < RT; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) T[(4 * tr + r) * ncp + 4 * tc + c] = acc[r][c];
+    for (int c = 0; c < 4; ++c) T[(RT * tr + r) * ncp + 4 * tc + c] = acc[r][c];
   __syncthreads();
   {
     const int dj = nthr / ny, db = nthr - dj * ny;
@@ -399,12 +405,12 @@ __global__ void k_slab_xy(const float* __restrict__ in, float* __restrict__ out,
     }
   }
   __syncthreads();
-  float acc2[4][4] = {};
+  float acc2[RT][4] = {};
   smem_mm(A1, nyp, T, ncp, ny, tr, tc, acc2);       // out[b][a] = sum_j M2[b][j] T[j][a]
   float* outk = out + (int64_t)blockIdx.x * nx * ny;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int b = 4 * tr + r;
+  for (int r = 0; r < RT; ++r) {
+    const int b = RT * tr + r;
     if (b >= ny) continue;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -419,7 +425,7 @@ __global__ void k_slab_xy(const float* __restrict__ in, float* __restrict__ out,
 __global__ void k_col_z(const float* __restrict__ in, float* __restrict__ out, TpfDev<float> tp) {
   extern __shared__ __align__(16) float sm[];
   const int nx = tp.n[0], ny = tp.n[1], nz = tp.n[2];
-  const int nzp = up4(nz);
+  const int nzp = up8(nz);
   const int64_t Q = (int64_t)nx * ny;
   const int64_t q0 = (int64_t)blockIdx.x * kColGroup;
   float* X = sm;                        // in tile   [nz][64]
@@ -446,11 +452,11 @@ __global__ void k_col_z(const float* __restrict__ in, float* __restrict__ out, T
     }
   }
   __syncthreads();
-  float acc[4][4] = {};
+  float acc[RT][4] = {};
   smem_mm(Mz, nzp, X, kColGroup, nz, tr, tc, acc);   // t[c][q] = sum_k Ez^-1[c][k] in[k][q]
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int c = 4 * tr + r;
+  for (int r = 0; r < RT; ++r) {
+    const int c = RT * tr + r;
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
       const int64_t q = q0 + 4 * tc + cc;
@@ -477,11 +483,11 @@ __global__ void k_col_z(const float* __restrict__ in, float* __restrict__ out, T
     }
   }
   __syncthreads();
-  float acc2[4][4] = {};
+  float acc2[RT][4] = {};
   smem_mm(Mz, nzp, Tt, kColGroup, nz, tr, tc, acc2);  // out[m][q] = sum_c Ez[m][c] t[c][q]
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int m = 4 * tr + r;
+  for (int r = 0; r < RT; ++r) {
+    const int m = RT * tr + r;
     if (m >= nz) continue;
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
@@ -498,11 +504,11 @@ inline int slab_cols(int nx) { return (nx + kSlabSplit - 1) / kSlabSplit; }
 inline size_t slab_smem(int nx, int ny) {
   const int nmax = nx > ny ? nx : ny;
   const int ncp = up4(slab_cols(nx));
-  return sizeof(float) * ((size_t)nmax * up4(ny) + (size_t)nx * ncp + (size_t)up4(ny) * ncp);
+  return sizeof(float) * ((size_t)nmax * up8(ny) + (size_t)nx * ncp + (size_t)up8(ny) * ncp);
 }
 
 inline size_t col_smem(int nz) {
-  return sizeof(float) * ((size_t)nz * kColGroup + (size_t)nz * up4(nz) + (size_t)up4(nz) * kColGroup);
+  return sizeof(float) * ((size_t)nz * kColGroup + (size_t)nz * up8(nz) + (size_t)up8(nz) * kColGroup);
 }
 
 fv_status tpf_fused_f32(const fv_grid* g, const float* r, float* phi) {
@@ -517,9 +523,9 @@ fv_status tpf_fused_f32(const fv_grid* g, const float* r, float* phi) {
     FV_CUDA(cudaFuncSetAttribute(k_col_z, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  const int slab_threads = ((ny + 3) / 4) * (up4(slab_cols(nx)) / 4);
+  const int slab_threads = (up8(ny) / RT) * (up4(slab_cols(nx)) / 4);
   const dim3 slab_grid(nz, kSlabSplit);
-  const int col_threads = ((nz + 3) / 4) * 16;
+  const int col_threads = (up8(nz) / RT) * 16;
   const unsigned ncol = (unsigned)(((int64_t)nx * ny + kColGroup - 1) / kColGroup);
   {
     LaunchScope ls_(g, FV_K_TPF_X);
@@ -580,12 +586,12 @@ fv_status tpf_one_transform_f32(const fv_grid* g, int axis) {
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
     if (axis == 0) {
       LaunchScope ls_(g, FV_K_TPF_X);
-      k_slab_xy<<<dim3(nz, kSlabSplit), ((ny + 3) / 4) * (up4(slab_cols(nx)) / 4),
+      k_slab_xy<<<dim3(nz, kSlabSplit), (up8(ny) / RT) * (up4(slab_cols(nx)) / 4),
                   slab_smem(nx, ny), g->stream>>>(a, b, g->tpf_f.Einvt[0], g->tpf_f.Einvt[1], nx,
                                                   ny, slab_cols(nx));
     } else {
       LaunchScope ls_(g, FV_K_TPF_YZ);
-      k_col_z<<<(unsigned)(((int64_t)nx * ny + kColGroup - 1) / kColGroup), ((nz + 3) / 4) * 16,
+      k_col_z<<<(unsigned)(((int64_t)nx * ny + kColGroup - 1) / kColGroup), (up8(nz) / RT) * 16,
                 col_smem(nz), g->stream>>>(a, b, g->tpf_f);
     }
     FV_CHECK_LAUNCH();

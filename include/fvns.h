@@ -186,6 +186,34 @@ fv_status arnoldi_leading(const fv_grid* g, const double* U, const double* v0,
                           int m, int nev, double* lam_re, double* lam_im, double* evec,
                           const fv_arnoldi_opts* opts, fv_arnoldi_stats* stats);
 
+/* Options / statistics of the critical-Re search. */
+typedef struct {
+  double rtol;        /* stop when |Re_{k+1} - Re_k| <= rtol Re_{k+1}       [1e-8] */
+  int max_iter;       /* secant steps after the two starting points          [30] */
+  int m, nev;         /* Arnoldi Krylov dimension / eigenvalues          [30, 4] */
+  int prec;           /* fv_prec of the Krylov vectors              [FV_FP64 = 0] */
+  double newton_tol;  /* ||F||_inf of each steady state                  [1e-10] */
+  double arnoldi_tol; /* Ritz tolerance                                  [1e-10] */
+} fv_critical_opts;
+
+typedef struct {
+  int evaluations;        /* sigma(Re) evaluations (Newton + Arnoldi)    */
+  double re_hist[64];     /* Re of each evaluation                       */
+  double sigma_hist[64];  /* real part of the leading eigenvalue         */
+  double omega_hist[64];  /* |imaginary part| of the leading eigenvalue  */
+} fv_critical_stats;
+
+/* Section 3: the critical Reynolds number, where the real part of the
+ * leading eigenvalue Lambda (largest real part) crosses zero, and the
+ * critical circular frequency omega_cr ~ |Im Lambda|.  Secant iteration on
+ * sigma(Re) = Re(Lambda(Re)) from re0 and re1 (the paper does not say how it
+ * brackets Re_cr).  Each evaluation sets the grid's Re, runs newton_steady
+ * warm-started from U, P (in: a steady state near re0; out: the steady
+ * state at Re_cr) and arnoldi_leading from v0.  re_cr / omega_cr: host. */
+fv_status fv_critical_re(fv_grid* g, double* U, double* P, const double* v0, double re0, double re1,
+                         const fv_critical_opts* opts, double* re_cr, double* omega_cr,
+                         fv_critical_stats* stats);
+
 /* W-weighted inner product <a, b> = sum over velocity faces of the momentum
  * control-volume size times a b (wall faces excluded).  Result to host. */
 fv_status fv_dot_w(const fv_grid* g, const double* a, const double* b, double* out /* host */);

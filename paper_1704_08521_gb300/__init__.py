@@ -177,6 +177,31 @@ def arnoldi_leading(g, U, v0, m=30, nev=5, evec=None, tol=1e-10, max_restarts=50
                  "ritz_resid": list(s.ritz_resid[:nev])}
 
 
+class fv_critical_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("m", ctypes.c_int),
+                ("nev", ctypes.c_int), ("prec", ctypes.c_int), ("newton_tol", ctypes.c_double),
+                ("arnoldi_tol", ctypes.c_double)]
+
+
+class fv_critical_stats(ctypes.Structure):
+    _fields_ = [("evaluations", ctypes.c_int), ("re_hist", ctypes.c_double * 64),
+                ("sigma_hist", ctypes.c_double * 64), ("omega_hist", ctypes.c_double * 64)]
+
+
+def fv_critical_re(g, U, P, v0, re0, re1, rtol=1e-8, max_iter=30, m=30, nev=4, prec="fp64",
+                   newton_tol=1e-10, arnoldi_tol=1e-10):
+    """Secant search of Re_cr (Section 3); returns (re_cr, omega_cr, history)."""
+    o = fv_critical_opts(rtol, max_iter, m, nev, PRECS.get(prec, prec), newton_tol, arnoldi_tol)
+    s = fv_critical_stats()
+    rc, om = ctypes.c_double(), ctypes.c_double()
+    check(lib.fv_critical_re(g.handle, _f64(U, g.n_vel, "U"), _f64(P, g.n_cell, "P"),
+                             _f64(v0, g.n_vel, "v0"), ctypes.c_double(re0), ctypes.c_double(re1),
+                             ctypes.byref(o), ctypes.byref(rc), ctypes.byref(om), ctypes.byref(s)),
+          "fv_critical_re")
+    k = min(s.evaluations, 64)
+    return rc.value, om.value, [(s.re_hist[i], s.sigma_hist[i], s.omega_hist[i]) for i in range(k)]
+
+
 def fv_dot_w(g, a, b):
     out = ctypes.c_double()
     check(lib.fv_dot_w(g.handle, _f64(a, g.n_vel, "a"), _f64(b, g.n_vel, "b"), ctypes.byref(out)),

@@ -41,6 +41,7 @@ _SIGS = {
     "newton_steady": (_I, [_P, _P, _P, _P, _P]),
     "arnoldi_leading": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P]),
     "fv_dot_w": (_I, [_P, _P, _P, _P]),
+    "fv_critical_re": (_I, [_P, _P, _P, _P, _D, _D, _P, _P, _P, _P]),
     "fv_pressure_solve": (_I, [_P, _P, _P, _I]),
     "fv_pressure_solve_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P]),
     "fv_profile_enable": (_I, [_P, _I]),

@@ -809,4 +809,67 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
   return FV_ENOCONV;
 }
 
+// --------------------------------------------------------- critical Re --
+fv_status fv_critical_re(fv_grid* g, double* U, double* P, const double* v0, double re0, double re1,
+                         const fv_critical_opts* opts, double* re_cr, double* omega_cr,
+                         fv_critical_stats* stats) {
+  FV_TRY(check_grid(g, "fv_critical_re"));
+  if (!U || !P || !v0 || !re_cr || !omega_cr || !(re0 > 0) || !(re1 > 0) || re0 == re1) {
+    set_error("fv_critical_re: bad argument");
+    return FV_EINVAL;
+  }
+  fv_critical_opts o = {};
+  if (opts) o = *opts;
+  if (o.rtol <= 0) o.rtol = 1e-8;
+  if (o.max_iter <= 0) o.max_iter = 30;
+  if (o.m <= 0) o.m = 30;
+  if (o.nev <= 0) o.nev = 4;
+  if (o.newton_tol <= 0) o.newton_tol = 1e-10;
+  if (o.arnoldi_tol <= 0) o.arnoldi_tol = 1e-10;
+  fv_critical_stats st = {};
+  fv_newton_opts no = {};
+  no.tol = o.newton_tol;
+  no.prec = o.prec;
+  fv_arnoldi_opts ao = {};
+  ao.tol = o.arnoldi_tol;
+  ao.prec = o.prec;
+  std::vector<double> lr(o.nev), li(o.nev);
+  // sigma(Re): Newton from the current U, P, then the leading eigenvalue
+  auto sigma = [&](double re, double* s, double* w) -> fv_status {
+    FV_TRY(fv_grid_set_re(g, re));
+    FV_TRY(newton_steady(g, U, P, &no, nullptr));
+    FV_TRY(arnoldi_leading(g, U, v0, o.m, o.nev, lr.data(), li.data(), nullptr, &ao, nullptr));
+    *s = lr[0];
+    *w = std::fabs(li[0]);
+    if (st.evaluations < 64) {
+      st.re_hist[st.evaluations] = re;
+      st.sigma_hist[st.evaluations] = *s;
+      st.omega_hist[st.evaluations] = *w;
+    }
+    ++st.evaluations;
+    return FV_OK;
+  };
+  double s0, w0, s1, w1;
+  fv_status rc = sigma(re0, &s0, &w0);
+  if (rc == FV_OK) rc = sigma(re1, &s1, &w1);
+  double a = re0, b = re1;
+  fv_status out = FV_ENOCONV;
+  for (int it = 0; rc == FV_OK && it < o.max_iter; ++it) {
+    if (s1 == s0) { set_error("fv_critical_re: flat secant"); out = FV_ENOCONV; break; }
+    const double c = b - s1 * (b - a) / (s1 - s0);
+    a = b;
+    s0 = s1;
+    b = c;
+    rc = sigma(b, &s1, &w1);
+    if (rc != FV_OK) break;
+    if (std::fabs(b - a) <= o.rtol * std::fabs(b)) { out = FV_OK; break; }
+  }
+  if (stats) *stats = st;
+  if (rc != FV_OK) return rc;
+  *re_cr = b;
+  *omega_cr = w1;
+  if (out != FV_OK) set_error("fv_critical_re: no convergence within max_iter");
+  return out;
+}
+
 }  // extern "C"

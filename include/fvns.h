@@ -214,6 +214,32 @@ fv_status fv_critical_re(fv_grid* g, double* U, double* P, const double* v0, dou
                          const fv_critical_opts* opts, double* re_cr, double* omega_cr,
                          fv_critical_stats* stats);
 
+/* ------------------------------------------------------------ batching --
+ * Several instances (grids of uneven sizes, Reynolds numbers and lid
+ * angles, e.g. the bracketing points of a critical-Re search) advance one
+ * mixed-precision Krylov-vector evaluation each in ONE CUDA graph launch:
+ * the momentum predictors of all instances in one persistent work-queue
+ * kernel, then the SIMPLE loops as concurrent graph branches, each with a
+ * device-side WHILE node.  The batch borrows the grids (their workspace and
+ * Re at capture time; create the batch after fv_grid_set_re).  The graph is
+ * captured on the first fv_batch_krylov call (outside any stream capture). */
+typedef struct fv_batch fv_batch;
+fv_status fv_batch_create(int n /* 1..32 */, fv_grid* const* grids /* host array */,
+                          void* cuda_stream, fv_batch** out);
+void fv_batch_destroy(fv_batch* b);
+/* out[i] = P (L_{U[i]} x[i] + sigma x[i]) - sigma x[i] for every instance
+ * (host arrays of device pointers; Eqs. 8-10 with the stop test of
+ * simple_krylov_solve, tolerance eps).  passes (host, n, optional): SIMPLE
+ * passes per instance; when given, the call synchronises and reports
+ * FV_ENOCONV / FV_ENAN of any instance. */
+fv_status fv_batch_krylov(fv_batch* b, const double* const* U, const double* const* x,
+                          double* const* out, double eps, double sigma, int* passes);
+/* Time the batched momentum kernel with 1, 2, 4, 8 z-planes per work item
+ * (ms: host, 4 entries, optional) and keep the fastest (returned in *best). */
+fv_status fv_batch_autotune(fv_batch* b, int* best, double* ms);
+/* Set the z-planes per work item explicitly (e.g. from a cached tuning). */
+fv_status fv_batch_set_tile(fv_batch* b, int planes);
+
 /* W-weighted inner product <a, b> = sum over velocity faces of the momentum
  * control-volume size times a b (wall faces excluded).  Result to host. */
 fv_status fv_dot_w(const fv_grid* g, const double* a, const double* b, double* out /* host */);

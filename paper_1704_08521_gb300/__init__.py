@@ -248,3 +248,63 @@ def fv_bench_kernel(g, kind, reps=50):
     check(lib.fv_bench_kernel(g.handle, KERNEL_KINDS.index(kind), reps, ctypes.byref(ms)),
           "fv_bench_kernel")
     return ms.value
+
+
+class Batch:
+    """Several grids advancing one Krylov-vector evaluation each per graph
+    launch (fv_batch_* in include/fvns.h)."""
+
+    def __init__(self, grids, stream=None):
+        arr = (ctypes.c_void_p * len(grids))(*[g.handle.value for g in grids])
+        h = ctypes.c_void_p()
+        st = _stream() if stream is None else ctypes.c_void_p(stream)
+        check(lib.fv_batch_create(len(grids), arr, st, ctypes.byref(h)), "fv_batch_create")
+        self.handle, self.grids = h, list(grids)
+
+    def krylov(self, U, x, out, eps=1e-8, sigma=0.0, sync=True):
+        n = len(self.grids)
+        pu = (ctypes.c_void_p * n)(*[_f64(U[i], self.grids[i].n_vel, "U").value for i in range(n)])
+        px = (ctypes.c_void_p * n)(*[_f64(x[i], self.grids[i].n_vel, "x").value for i in range(n)])
+        po = (ctypes.c_void_p * n)(*[_f64(out[i], self.grids[i].n_vel, "out").value for i in range(n)])
+        passes = (ctypes.c_int * n)() if sync else None
+        check(lib.fv_batch_krylov(self.handle, pu, px, po, ctypes.c_double(eps), ctypes.c_double(sigma),
+                                  passes), "fv_batch_krylov")
+        return list(passes) if sync else None
+
+    def autotune(self, cache=None):
+        """Pick the z-planes per work item of the batched momentum kernel:
+        from the JSON cache when this batch shape was tuned before, else by
+        timing the candidates (fv_batch_autotune) and recording the winner."""
+        import json
+        path = cache or os.environ.get("FVNS_AUTOTUNE_CACHE") or os.path.join(
+            os.path.expanduser("~"), ".cache", "fvns_autotune.json")
+        key = "k_batch_jv|" + ";".join(f"{g.shape}|{g.re}" for g in self.grids)
+        try:
+            table = json.load(open(path))
+        except (OSError, ValueError):
+            table = {}
+        if key in table:
+            check(lib.fv_batch_set_tile(self.handle, int(table[key]["planes"])), "fv_batch_set_tile")
+            return table[key]
+        best = ctypes.c_int()
+        ms = (ctypes.c_double * 4)()
+        check(lib.fv_batch_autotune(self.handle, ctypes.byref(best), ms), "fv_batch_autotune")
+        entry = {"planes": best.value, "ms": {str(p): ms[i] for i, p in enumerate((1, 2, 4, 8))}}
+        table[key] = entry
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            json.dump(table, open(path, "w"), indent=1)
+        except OSError:
+            pass
+        return entry
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.fv_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -41,6 +41,11 @@ _SIGS = {
     "newton_steady": (_I, [_P, _P, _P, _P, _P]),
     "arnoldi_leading": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P]),
     "fv_dot_w": (_I, [_P, _P, _P, _P]),
+    "fv_batch_create": (_I, [_I, _P, _P, ctypes.POINTER(_P)]),
+    "fv_batch_destroy": (None, [_P]),
+    "fv_batch_krylov": (_I, [_P, _P, _P, _P, _D, _D, _P]),
+    "fv_batch_autotune": (_I, [_P, _P, _P]),
+    "fv_batch_set_tile": (_I, [_P, _I]),
     "fv_critical_re": (_I, [_P, _P, _P, _P, _D, _D, _P, _P, _P, _P]),
     "fv_pressure_solve": (_I, [_P, _P, _P, _I]),
     "fv_pressure_solve_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P]),

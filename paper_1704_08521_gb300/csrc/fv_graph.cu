@@ -17,6 +17,7 @@
 
 #include "fv_ff.cuh"
 #include "fv_internal.cuh"
+#include "fv_stencil_dev.cuh"
 
 namespace fv {
 
@@ -420,7 +421,432 @@ void destroy_graph_cache(GraphCache& c) {
   c = GraphCache();
 }
 
+
+// ===========================================================================
+// Batched instances: several grids (uneven sizes, Reynolds numbers, lid
+// angles) advance one Krylov-vector evaluation each in ONE graph launch.
+// The momentum predictors of all instances are computed by a persistent
+// work-queue kernel (blocks pull (instance, z-tile) items from an atomic
+// counter, so small and large grids share the SMs); the SIMPLE loops then run
+// as concurrent graph branches, one WHILE conditional node per instance.  The
+// z-tile depth (planes per work item) is picked by fv_batch_autotune.
+namespace {
+
+constexpr int kBatchMax = 32;
+constexpr int kBatchBlocks = 152 * 4;
+
+struct BatchCall {
+  const double* U[kBatchMax];
+  const double* x[kBatchMax];
+  double* out[kBatchMax];
+  float eps, sigma;
+  int n;
+};
+
+struct InstDesc {
+  Met<float> m;
+  const float* U32;
+  const float* x32;
+  float* w32;
+  float inv_re;
+  int tile_base;
+};
+
+__global__ void k_batch_init(BatchCall bc, CallBlock* dcb, LoopState* dls) {
+  const int i = threadIdx.x;
+  if (i >= bc.n) return;
+  CallBlock c;
+  c.U = bc.U[i];
+  c.x = bc.x[i];
+  c.out = bc.out[i];
+  c.p = nullptr;
+  c.sigma = bc.sigma;
+  c.eps = bc.eps;
+  c.omega = 1.f;
+  c.max_pass = 200;
+  dcb[i] = c;
+  LoopState& l = dls[i];
+  l.phi1 = l.phi_prev = l.phi_last = l.div_last = 0.f;
+  l.pass = l.nan = l.status = 0;
+}
+
+// Momentum predictor (Eq. 10, float32) of every instance: blocks pull work
+// items (instance, ppt consecutive z-planes) from an atomic counter.
+__global__ void __launch_bounds__(256) k_batch_jv(const InstDesc* __restrict__ d, int ninst,
+                                                  int total, int ppt, float shift,
+                                                  unsigned* __restrict__ counter) {
+  __shared__ int s_tile;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= total) return;
+    int inst = 0;
+    while (inst + 1 < ninst && d[inst + 1].tile_base <= tile) ++inst;
+    const Met<float> m = d[inst].m;
+    const float* U = d[inst].U32;
+    const float* V = d[inst].x32;
+    float* out = d[inst].w32;
+    const float inv_re = d[inst].inv_re;
+    const int z0 = (tile - d[inst].tile_base) * ppt;
+    const int nx = m.n[0], ny = m.n[1], nz = m.n[2];
+    const int plane = nx * ny;
+    const int nc = (int)m.ncell;
+    const int st[3] = {1, nx, plane};
+    for (int t = threadIdx.x; t < plane; t += blockDim.x) {
+      const int i = t % nx, j = t / nx;
+      for (int kk = 0; kk < ppt; ++kk) {
+        const int k = z0 + kk;
+        if (k >= nz) break;
+        const int pos[3] = {i, j, k};
+        const int base = k * plane + t;
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+        if (i > 0)
+          r0 = stencil::momentum_face<float, 0, true, float>(m, U, V, base, pos, st, inv_re, 0.f, shift);
+        if (j > 0)
+          r1 = stencil::momentum_face<float, 1, true, float>(m, U, V, base, pos, st, inv_re, 0.f, shift);
+        if (k > 0)
+          r2 = stencil::momentum_face<float, 2, true, float>(m, U, V, base, pos, st, inv_re, 0.f, shift);
+        out[base] = r0;
+        out[nc + base] = r1;
+        out[2 * nc + base] = r2;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+struct BatchImpl {
+  int n = 0;
+  int ppt = 1;
+  double sigma = 0.0;
+  fv_grid* grids[kBatchMax] = {};
+  cudaStream_t stream = nullptr;
+  CallBlock* d_call = nullptr;
+  LoopState* d_loop = nullptr;
+  InstDesc* d_desc = nullptr;
+  unsigned* d_counter = nullptr;
+  int total_tiles = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t init_node = nullptr;
+  bool ready = false;
+};
+
+static fv_status batch_descriptors(BatchImpl& b) {
+  std::vector<InstDesc> h(b.n);
+  int base = 0;
+  for (int i = 0; i < b.n; ++i) {
+    fv_grid* g = b.grids[i];
+    h[i].m = g->met_f;
+    h[i].U32 = g->U32;
+    h[i].x32 = g->x32;
+    h[i].w32 = g->w32;
+    h[i].inv_re = float(1.0 / g->re);
+    h[i].tile_base = base;
+    base += (g->n[2] + b.ppt - 1) / b.ppt;
+  }
+  b.total_tiles = base;
+  FV_CUDA(cudaMemcpy(b.d_desc, h.data(), b.n * sizeof(InstDesc), cudaMemcpyHostToDevice));
+  return FV_OK;
+}
+
+static fv_status launch_batch_jv(BatchImpl& b, cudaStream_t s) {
+  FV_CUDA(cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned), s));
+  const int blocks = std::min(kBatchBlocks, b.total_tiles);
+  count_launch();
+  k_batch_jv<<<blocks, 256, 0, s>>>(b.d_desc, b.n, b.total_tiles, b.ppt, float(b.sigma), b.d_counter);
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+static void batch_release_graph(BatchImpl& b) {
+  if (b.exec) cudaGraphExecDestroy(b.exec);
+  if (b.graph) cudaGraphDestroy(b.graph);
+  b.exec = nullptr;
+  b.graph = nullptr;
+  b.ready = false;
+}
+
+// Capture the batch graph: init -> round (per instance) -> batched J.v ->
+// per-instance branches {D w -> TPF -> correct -> decide -> WHILE{...} -> join}.
+static fv_status batch_build_graph(BatchImpl& b) {
+  batch_release_graph(b);
+  FV_TRY(batch_descriptors(b));
+  cudaStream_t cs;
+  FV_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  std::vector<cudaStream_t> ss(b.n), bs(b.n);
+  std::vector<cudaEvent_t> ev(b.n + 1);
+  for (int i = 0; i < b.n; ++i) {
+    FV_CUDA(cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking));
+    FV_CUDA(cudaStreamCreateWithFlags(&bs[i], cudaStreamNonBlocking));
+  }
+  for (auto& e : ev) FV_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  std::vector<cudaStream_t> saved(b.n);
+  for (int i = 0; i < b.n; ++i) {
+    saved[i] = b.grids[i]->stream;
+    b.grids[i]->capturing = true;
+  }
+  fv_status st = FV_OK;
+  cudaGraph_t graph = nullptr;
+  auto cleanup = [&]() {
+    for (int i = 0; i < b.n; ++i) {
+      b.grids[i]->stream = saved[i];
+      b.grids[i]->capturing = false;
+      cudaStreamDestroy(ss[i]);
+      cudaStreamDestroy(bs[i]);
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    cudaStreamDestroy(cs);
+  };
+#define BCHK(call)                                      \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      st = cuda_fail(e_, #call, __FILE__, __LINE__);    \
+      cudaStreamEndCapture(cs, &graph);                 \
+      if (graph) cudaGraphDestroy(graph);               \
+      (void)cudaGetLastError();                         \
+      cleanup();                                        \
+      return st;                                        \
+    }                                                   \
+  } while (0)
+#define BTRY(call)                                      \
+  do {                                                  \
+    fv_status s_ = (call);                              \
+    if (s_ != FV_OK) {                                  \
+      cudaStreamEndCapture(cs, &graph);                 \
+      if (graph) cudaGraphDestroy(graph);               \
+      (void)cudaGetLastError();                         \
+      cleanup();                                        \
+      return s_;                                        \
+    }                                                   \
+  } while (0)
+  BCHK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  BatchCall bc = {};
+  k_batch_init<<<1, kBatchMax, 0, cs>>>(bc, b.d_call, b.d_loop);
+  BCHK(cudaGetLastError());
+  for (int i = 0; i < b.n; ++i) {
+    fv_grid* g = b.grids[i];
+    k_round2<<<grid1d(g->nvel), 256, 0, cs>>>(b.d_call + i, g->U32, g->x32, g->nvel);
+    BCHK(cudaGetLastError());
+  }
+  BTRY(launch_batch_jv(b, cs));
+  BCHK(cudaEventRecord(ev[b.n], cs));
+  for (int i = 0; i < b.n; ++i) {
+    fv_grid* g = b.grids[i];
+    cudaStream_t s = ss[i];
+    BCHK(cudaStreamWaitEvent(s, ev[b.n], 0));
+    g->stream = s;
+    const int bx = kCellThreads;
+    const dim3 cg = cell_launch_grid(g->n);
+    const int64_t nb = (int64_t)cg.x * cg.y * cg.z;
+    float* part = (float*)g->d_part;
+    const CallBlock* dcb = b.d_call + i;
+    LoopState* dls = b.d_loop + i;
+    BTRY(launch_div_f32(g, g->w32, g->r32));
+    BTRY(tpf_solve_f32(g, g->r32, g->phi32));
+    k_correct_g<true><<<cg, bx, 0, s>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32, g->pff,
+                                        g->r32, dcb, dls, part);
+    BCHK(cudaGetLastError());
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cap;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    BCHK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cap, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle h;
+    BCHK(cudaGraphConditionalHandleCreate(&h, cap, 1, cudaGraphCondAssignDefault));
+    k_decide<<<1, 1024, 0, s>>>(part, nb, dls, dcb, h, 1);
+    BCHK(cudaGetLastError());
+    BCHK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cap, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    BCHK(cudaGraphAddNode(&cnode, cap, deps, nullptr, nd, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    BCHK(cudaStreamBeginCaptureToGraph(bs[i], body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal));
+    g->stream = bs[i];
+    fv_status s2 = tpf_solve_f32(g, g->r32, g->phi32);
+    if (s2 == FV_OK) {
+      k_correct_g<false><<<cg, bx, 0, bs[i]>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32,
+                                               g->pff, g->r32, dcb, dls, part);
+      k_decide<<<1, 1024, 0, bs[i]>>>(part, nb, dls, dcb, h, 1);
+    }
+    cudaGraph_t bg = body;
+    cudaError_t e2 = cudaStreamEndCapture(bs[i], &bg);
+    g->stream = s;
+    BTRY(s2);
+    BCHK(e2);
+    BCHK(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    k_join_g<<<grid1d(g->nvel), 256, 0, s>>>(g->vff[0], g->vff[1], g->pff, dls, dcb, g->nvel,
+                                             g->ncell);
+    BCHK(cudaGetLastError());
+    BCHK(cudaEventRecord(ev[i], s));
+    BCHK(cudaStreamWaitEvent(cs, ev[i], 0));
+  }
+  BCHK(cudaStreamEndCapture(cs, &graph));
+#undef BCHK
+#undef BTRY
+  cleanup();
+  size_t nroot = 0;
+  FV_CUDA(cudaGraphGetRootNodes(graph, nullptr, &nroot));
+  std::vector<cudaGraphNode_t> roots(nroot);
+  FV_CUDA(cudaGraphGetRootNodes(graph, roots.data(), &nroot));
+  if (nroot != 1) {
+    cudaGraphDestroy(graph);
+    set_error("batch graph: unexpected root count");
+    return FV_ECUDA;
+  }
+  b.init_node = roots[0];
+  FV_CUDA(cudaGraphInstantiate(&b.exec, graph, 0));
+  b.graph = graph;
+  b.ready = true;
+  return FV_OK;
+}
+
 }  // namespace fv
+
+struct fv_batch {
+  fv::BatchImpl impl;
+};
+
+using namespace fv;
+
+extern "C" {
+
+fv_status fv_batch_set_tile(fv_batch* b, int ppt);
+
+fv_status fv_batch_create(int n, fv_grid* const* grids, void* cuda_stream, fv_batch** out) {
+  if (!out || !grids || n < 1 || n > kBatchMax) {
+    set_error("fv_batch_create: need 1..32 grids");
+    return FV_EINVAL;
+  }
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!grids[i]) { set_error("fv_batch_create: NULL grid"); return FV_EINVAL; }
+  fv_batch* b = new fv_batch();
+  BatchImpl& B = b->impl;
+  B.n = n;
+  for (int i = 0; i < n; ++i) B.grids[i] = grids[i];
+  B.stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_call, kBatchMax * sizeof(CallBlock));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_loop, kBatchMax * sizeof(LoopState));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_desc, kBatchMax * sizeof(InstDesc));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_counter, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+    fv_batch_destroy(b);
+    return FV_ENOMEM;
+  }
+  *out = b;
+  return FV_OK;
+}
+
+void fv_batch_destroy(fv_batch* b) {
+  if (!b) return;
+  BatchImpl& B = b->impl;
+  batch_release_graph(B);
+  void* ptrs[] = {B.d_call, B.d_loop, B.d_desc, B.d_counter};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete b;
+}
+
+fv_status fv_batch_krylov(fv_batch* b, const double* const* U, const double* const* x,
+                          double* const* out, double eps, double sigma, int* passes) {
+  if (!b || !U || !x || !out) { set_error("fv_batch_krylov: NULL argument"); return FV_EINVAL; }
+  BatchImpl& B = b->impl;
+  if (!(eps > 0) || sigma < 0) { set_error("fv_batch_krylov: bad eps/sigma"); return FV_EINVAL; }
+  BatchCall bc = {};
+  for (int i = 0; i < B.n; ++i) {
+    if (!U[i] || !x[i] || !out[i] || x[i] == out[i]) {
+      set_error("fv_batch_krylov: bad pointer");
+      return FV_EINVAL;
+    }
+    bc.U[i] = U[i];
+    bc.x[i] = x[i];
+    bc.out[i] = out[i];
+  }
+  bc.n = B.n;
+  bc.eps = (float)eps;
+  bc.sigma = (float)sigma;
+  if (!B.ready || B.sigma != sigma) {
+    B.sigma = sigma;
+    FV_TRY(batch_build_graph(B));
+  }
+  void* dcb = B.d_call;
+  void* dls = B.d_loop;
+  void* args[3] = {&bc, &dcb, &dls};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)k_batch_init;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(kBatchMax);
+  kp.kernelParams = args;
+  FV_CUDA(cudaGraphExecKernelNodeSetParams(B.exec, B.init_node, &kp));
+  count_launch();
+  FV_CUDA(cudaGraphLaunch(B.exec, B.stream));
+  if (passes) {
+    std::vector<LoopState> h(B.n);
+    FV_CUDA(cudaMemcpyAsync(h.data(), B.d_loop, B.n * sizeof(LoopState), cudaMemcpyDeviceToHost,
+                            B.stream));
+    FV_CUDA(cudaStreamSynchronize(B.stream));
+    for (int i = 0; i < B.n; ++i) passes[i] = h[i].pass;
+    for (int i = 0; i < B.n; ++i)
+      if (h[i].status != 1) {
+        set_error("fv_batch_krylov: an instance did not converge");
+        return h[i].status == 3 ? FV_ENAN : FV_ENOCONV;
+      }
+  }
+  return FV_OK;
+}
+
+fv_status fv_batch_autotune(fv_batch* b, int* best_ppt, double* ms) {
+  if (!b || !best_ppt) { set_error("fv_batch_autotune: NULL argument"); return FV_EINVAL; }
+  BatchImpl& B = b->impl;
+  static const int cand[4] = {1, 2, 4, 8};
+  cudaEvent_t e0, e1;
+  FV_CUDA(cudaEventCreate(&e0));
+  FV_CUDA(cudaEventCreate(&e1));
+  double best = 1e30;
+  int bp = 1;
+  for (int c = 0; c < 4; ++c) {
+    B.ppt = cand[c];
+    FV_TRY(batch_descriptors(B));
+    FV_TRY(launch_batch_jv(B, B.stream));          // warm-up
+    FV_CUDA(cudaEventRecord(e0, B.stream));
+    for (int r = 0; r < 10; ++r) FV_TRY(launch_batch_jv(B, B.stream));
+    FV_CUDA(cudaEventRecord(e1, B.stream));
+    FV_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    FV_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    if (ms) ms[c] = t / 10.0;
+    if (t < best) { best = t; bp = cand[c]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *best_ppt = bp;
+  B.ppt = 0;                                       // force the graph rebuild below
+  return fv_batch_set_tile(b, bp);
+}
+
+fv_status fv_batch_set_tile(fv_batch* b, int ppt) {
+  if (!b || ppt < 1 || ppt > 64) { set_error("fv_batch_set_tile: bad argument"); return FV_EINVAL; }
+  BatchImpl& B = b->impl;
+  if (B.ppt != ppt) {
+    B.ppt = ppt;
+    batch_release_graph(B);
+  }
+  return FV_OK;
+}
+
+}  // extern "C"
 
 extern "C" fv_status fv_bench_kernel(fv_grid* g, int kind, int reps, double* ms_per_launch) {
   if (!g || !ms_per_launch || reps < 1) { fv::set_error("fv_bench_kernel: bad argument"); return FV_EINVAL; }

@@ -55,11 +55,15 @@ typedef enum {
 typedef enum { FV_MAP_SINE0975 = 0, FV_MAP_COSINE = 1, FV_MAP_UNIFORM = 2 } fv_map;
 
 /* Arithmetic of the stencil and pressure-correction sweeps.
- * FV_FP64 : everything in float64.
- * FV_MIXED: J.v and the tensor-product pressure-correction solve in float32
- *           inside the float64 defect-correction loop of the SIMPLE-like
- *           algorithm; divergence, correction and norms in float64. */
-typedef enum { FV_FP64 = 0, FV_MIXED = 1 } fv_prec;
+ * FV_FP64 : everything in float64 (on GB300 the FP64 pipes run at ~1/70 of
+ *           the FP32 rate: this is the plain reference form).
+ * FV_MIXED: J.v and the tensor-product pressure-correction solve in float32;
+ *           the defect-correction state (velocity, pressure) and its
+ *           divergence in float-float (hi + lo float pairs, ~48 bits).
+ * FV_FF   : as FV_MIXED, but J.v also in float-float: results agree with
+ *           FV_FP64 to ~1e-12 relative, on the FP32 pipes (for eigenvalues
+ *           to 1e-7 and below).  Graph path only for simple_krylov_solve. */
+typedef enum { FV_FP64 = 0, FV_MIXED = 1, FV_FF = 2 } fv_prec;
 
 typedef struct fv_grid fv_grid; /* opaque: metrics, solver tables, workspace */
 

@@ -18,8 +18,8 @@ from ._lib import lib, FvError, check, STATUS_NAMES  # noqa: F401
 
 FV_MAP_SINE0975, FV_MAP_COSINE, FV_MAP_UNIFORM = 0, 1, 2
 MAPS = {"sine0975": FV_MAP_SINE0975, "cosine": FV_MAP_COSINE, "uniform": FV_MAP_UNIFORM}
-FV_FP64, FV_MIXED = 0, 1
-PRECS = {"fp64": FV_FP64, "mixed": FV_MIXED}
+FV_FP64, FV_MIXED, FV_FF = 0, 1, 2
+PRECS = {"fp64": FV_FP64, "mixed": FV_MIXED, "ff": FV_FF}
 
 
 class fv_grid_info(ctypes.Structure):

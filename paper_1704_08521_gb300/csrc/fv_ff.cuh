@@ -243,4 +243,26 @@ FF_HD ff ff_mul_f(ff x, float y) {
   return fast_two_sum(p, e);
 }
 
+// ---- a float-float number with arithmetic operators, so that the momentum
+// stencil template can run in ~48-bit arithmetic on the FP32 pipes
+struct ffn {
+  float hi, lo;
+  FF_HD ffn() : hi(0.f), lo(0.f) {}
+  FF_HD ffn(float a) : hi(a), lo(0.f) {}
+  FF_HD ffn(int a) : hi((float)a), lo(0.f) {}
+  FF_HD ffn(double a) : hi((float)a), lo(0.f) {}   // literals only (0, 0.5, 0.25)
+  FF_HD ffn(float a, float b) : hi(a), lo(b) {}
+#ifdef __CUDACC__
+  __host__ __device__ ffn(float2 a) : hi(a.x), lo(a.y) {}
+#endif
+  FF_HD ffn(ff a) : hi(a.hi), lo(a.lo) {}
+};
+
+FF_HD ffn operator+(ffn a, ffn b) { return ffn(ff_add({a.hi, a.lo}, {b.hi, b.lo})); }
+FF_HD ffn operator-(ffn a, ffn b) { return ffn(ff_sub({a.hi, a.lo}, {b.hi, b.lo})); }
+FF_HD ffn operator*(ffn a, ffn b) { return ffn(ff_mul({a.hi, a.lo}, {b.hi, b.lo})); }
+FF_HD ffn operator-(ffn a) { return ffn(-a.hi, -a.lo); }
+FF_HD ffn& operator+=(ffn& a, ffn b) { a = a + b; return a; }
+FF_HD ffn& operator-=(ffn& a, ffn b) { a = a - b; return a; }
+
 }  // namespace fv

@@ -54,6 +54,18 @@ __global__ void k_round2(const CallBlock* __restrict__ cb, float* __restrict__ U
   }
 }
 
+__global__ void k_split2_cb(const CallBlock* __restrict__ cb, float2* __restrict__ Uff,
+                            float2* __restrict__ xff, int64_t n) {
+  const double* U = cb->U;
+  const double* x = cb->x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const ff a = f64_split(__ldg(U + e)), b = f64_split(__ldg(x + e));
+    Uff[e] = make_float2(a.hi, a.lo);
+    xff[e] = make_float2(b.hi, b.lo);
+  }
+}
+
 __device__ __forceinline__ float block_maxf(float v) {
   __shared__ float red[32];
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -72,7 +84,7 @@ __device__ __forceinline__ float block_maxf(float v) {
 // One SIMPLE pass on the float-float state (see k_correct_ff in
 // fv_mixed.cu); buffers chosen by the number of completed passes.  Block
 // maxima of |phi| and |D v| go to per-block partials (no atomics).
-template <bool FIRST>
+template <bool FIRST, bool FFG = false>
 __global__ void __launch_bounds__(256) k_correct_g(MetFF m, const float* __restrict__ w32,
                                                    float2* vff0, float2* vff1,
                                                    const float* __restrict__ phi,
@@ -108,13 +120,23 @@ __global__ void __launch_bounds__(256) k_correct_g(MetFF m, const float* __restr
       const int q = pos[c];
       ff lo = {0.f, 0.f}, hi = {0.f, 0.f};
       if (q > 0) {
-        const float g = (f0 - __ldg(phi + base - st[c])) * m.idc[c][q];
-        lo = ff_add_f(load(c * nc + base), -omega * g);
+        if (FFG) {   // gradient of the float32 phi evaluated in float-float
+          const ff gr = ff_mul(two_sum(f0, -__ldg(phi + base - st[c])), of2(m.idcf[c][q]));
+          lo = ff_sub(load(c * nc + base), ff_mul_f(gr, omega));
+        } else {
+          const float g = (f0 - __ldg(phi + base - st[c])) * m.idc[c][q];
+          lo = ff_add_f(load(c * nc + base), -omega * g);
+        }
       }
       vout[c * nc + base] = to2(lo);
       if (q + 1 < m.n[c]) {
-        const float g = (__ldg(phi + base + st[c]) - f0) * m.idc[c][q + 1];
-        hi = ff_add_f(load(c * nc + base + st[c]), -omega * g);
+        if (FFG) {
+          const ff gr = ff_mul(two_sum(__ldg(phi + base + st[c]), -f0), of2(m.idcf[c][q + 1]));
+          hi = ff_sub(load(c * nc + base + st[c]), ff_mul_f(gr, omega));
+        } else {
+          const float g = (__ldg(phi + base + st[c]) - f0) * m.idc[c][q + 1];
+          hi = ff_add_f(load(c * nc + base + st[c]), -omega * g);
+        }
       }
       dv = ff_add(dv, ff_mul(ff_sub(hi, lo), of2(m.idx[c][q])));
     }
@@ -195,23 +217,11 @@ inline unsigned grid1d(int64_t n) {
 
 inline int block_x(const fv_grid*) { return kCellThreads; }
 
-// Record the evaluation on stream s (capturing); `h` valid when in the body.
-fv_status record_prefix(const fv_grid* g, cudaStream_t s, double sigma, GraphCache& gc) {
-  const int bx = block_x(g);
-  const dim3 cg = cell_launch_grid(g->n);
-  CallBlock cb = {};
-  k_call_init<<<1, 1, 0, s>>>(cb, (CallBlock*)gc.d_call, gc.d_loop);
-  FV_CHECK_LAUNCH();
-  k_round2<<<grid1d(g->nvel), 256, 0, s>>>((const CallBlock*)gc.d_call, g->U32, g->x32, g->nvel);
-  FV_CHECK_LAUNCH();
-  return FV_OK;
-}
-
 }  // namespace
 
 // Build (once per grid and shift) the executable graph of a mixed-precision
 // Krylov-vector evaluation.
-static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc) {
+static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc, int prec = FV_MIXED) {
   FV_CUDA(cudaMalloc(&gc.d_call, sizeof(CallBlock)));
   FV_CUDA(cudaMalloc((void**)&gc.d_loop, sizeof(LoopState)));
   cudaStream_t cs;
@@ -240,12 +250,29 @@ static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc) {
   const int64_t nb = (int64_t)cg.x * cg.y * cg.z;
   float* part = (float*)g->d_part;
   const CallBlock* dcb = (const CallBlock*)gc.d_call;
-  if ((st = record_prefix(g, cs, sigma, gc)) != FV_OK) return fail(st);
-  if ((st = launch_momentum_f32(g, g->U32, g->x32, g->w32, sigma)) != FV_OK) return fail(st);
-  if ((st = launch_div_f32(g, g->w32, g->r32)) != FV_OK) return fail(st);
-  if ((st = tpf_solve_f32(g, g->r32, g->phi32)) != FV_OK) return fail(st);
-  k_correct_g<true><<<cg, bx, 0, cs>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32, g->pff,
-                                       g->r32, dcb, gc.d_loop, part);
+  {
+    CallBlock cb0 = {};
+    k_call_init<<<1, 1, 0, cs>>>(cb0, (CallBlock*)gc.d_call, gc.d_loop);
+  }
+  if (prec == FV_FF) {
+    // float-float operands and J.v; the predictor lands in vff[1], which the
+    // first (non-initialising) pass reads, with p starting from zero
+    k_split2_cb<<<grid1d(g->nvel), 256, 0, cs>>>(dcb, g->Uff, g->xff, g->nvel);
+    if ((st = launch_momentum_ff(g, g->Uff, g->xff, g->vff[1], sigma)) != FV_OK) return fail(st);
+    if ((st = launch_div_ff(g, g->vff[1], g->r32)) != FV_OK) return fail(st);
+    if (cudaMemsetAsync(g->pff, 0, g->ncell * sizeof(float2), cs) != cudaSuccess)
+      return fail(cuda_fail(cudaGetLastError(), "cudaMemsetAsync", __FILE__, __LINE__));
+    if ((st = tpf_solve_f32(g, g->r32, g->phi32)) != FV_OK) return fail(st);
+    k_correct_g<false, true><<<cg, bx, 0, cs>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32,
+                                                g->pff, g->r32, dcb, gc.d_loop, part);
+  } else {
+    k_round2<<<grid1d(g->nvel), 256, 0, cs>>>(dcb, g->U32, g->x32, g->nvel);
+    if ((st = launch_momentum_f32(g, g->U32, g->x32, g->w32, sigma)) != FV_OK) return fail(st);
+    if ((st = launch_div_f32(g, g->w32, g->r32)) != FV_OK) return fail(st);
+    if ((st = tpf_solve_f32(g, g->r32, g->phi32)) != FV_OK) return fail(st);
+    k_correct_g<true><<<cg, bx, 0, cs>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32, g->pff,
+                                         g->r32, dcb, gc.d_loop, part);
+  }
   // the conditional handle belongs to the graph being captured
   cudaStreamCaptureStatus cst;
   cudaGraph_t cap_graph;
@@ -279,8 +306,12 @@ static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc) {
     g->stream = bs;
     fv_status s2 = tpf_solve_f32(g, g->r32, g->phi32);
     if (s2 == FV_OK) {
-      k_correct_g<false><<<cg, bx, 0, bs>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32,
-                                            g->pff, g->r32, dcb, gc.d_loop, part);
+      if (prec == FV_FF)
+        k_correct_g<false, true><<<cg, bx, 0, bs>>>(g->met_ff, g->w32, g->vff[0], g->vff[1],
+                                                    g->phi32, g->pff, g->r32, dcb, gc.d_loop, part);
+      else
+        k_correct_g<false><<<cg, bx, 0, bs>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32,
+                                              g->pff, g->r32, dcb, gc.d_loop, part);
       k_decide<<<1, 1024, 0, bs>>>(part, nb, gc.d_loop, dcb, h, 1);
     }
     cudaGraph_t bg = body;
@@ -310,6 +341,7 @@ static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc) {
   FV_CUDA(cudaGraphInstantiate(&gc.exec, graph, 0));
   gc.graph = graph;
   gc.sigma = sigma;
+  gc.prec = prec;
   gc.ready = true;
   return FV_OK;
 }
@@ -317,18 +349,18 @@ static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc) {
 fv_status mixed_krylov_graph(const fv_grid* gcst, const double* U, const double* x, double* out,
                              double* p, double sigma, double eps, int max_pass, double omega,
                              bool sync, int* passes, double* phi1, double* phil, double* divl,
-                             int* status) {
+                             int* status, int prec) {
   fv_grid* g = const_cast<fv_grid*>(gcst);
   GraphCache* gc = nullptr;
   for (auto& c : g->graphs)
-    if (c.ready && c.sigma == sigma) gc = &c;
+    if (c.ready && c.sigma == sigma && c.prec == prec) gc = &c;
   if (!gc) {
     GraphCache* slot = nullptr;
     for (auto& c : g->graphs)
       if (!c.ready) { slot = &c; break; }
     if (!slot) slot = &g->graphs[0];
     destroy_graph_cache(*slot);
-    FV_TRY(build_graph(g, sigma, *slot));
+    FV_TRY(build_graph(g, sigma, *slot, prec));
     gc = slot;
   }
   CallBlock cb;

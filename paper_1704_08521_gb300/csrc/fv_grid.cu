@@ -311,6 +311,42 @@ static fv_status build(fv_grid* g) {
     }
     g->met_ff.ncell = g->ncell;
   }
+  // float-float metrics (FV_FF J.v): idx, idc, th, dx, dc per axis, each
+  // value split exactly into (hi, lo)
+  {
+    size_t total = 0;
+    for (int d = 0; d < 3; ++d) total += 5 * (size_t)(g->n[d] + 1);
+    std::vector<float2> h(total, make_float2(0.f, 0.f));
+    size_t off[3], o = 0;
+    auto put = [](double v) { const ff s2 = f64_split(v); return make_float2(s2.hi, s2.lo); };
+    for (int d = 0; d < 3; ++d) {
+      const int n = g->n[d];
+      off[d] = o;
+      float2* q = h.data() + o;
+      for (int m = 0; m < n; ++m) q[m] = put(1.0 / g->h_dx[d][m]);
+      for (int f = 0; f <= n; ++f) q[(n + 1) + f] = put(1.0 / g->h_dc[d][f]);
+      for (int f = 1; f < n; ++f) q[2 * (n + 1) + f] = put(0.5 * g->h_dx[d][f - 1] / g->h_dc[d][f]);
+      for (int m = 0; m < n; ++m) q[3 * (n + 1) + m] = put(g->h_dx[d][m]);
+      for (int f = 0; f <= n; ++f) q[4 * (n + 1) + f] = put(g->h_dc[d][f]);
+      o += 5 * (size_t)(n + 1);
+    }
+    FV_TRY(alloc(g, &g->d_met_fn, total * sizeof(float2)));
+    FV_CUDA(cudaMemcpy(g->d_met_fn, h.data(), total * sizeof(float2), cudaMemcpyHostToDevice));
+    const ffn* base = (const ffn*)g->d_met_fn;
+    for (int d = 0; d < 3; ++d) {
+      const int n = g->n[d];
+      g->met_fn.n[d] = n;
+      g->met_fn.idx[d] = base + off[d];
+      g->met_fn.idc[d] = base + off[d] + (n + 1);
+      g->met_fn.th[d] = base + off[d] + 2 * (n + 1);
+      g->met_fn.dx[d] = base + off[d] + 3 * (n + 1);
+      g->met_fn.dc[d] = base + off[d] + 4 * (n + 1);
+    }
+    g->met_fn.ncell = g->ncell;
+    for (int d = 0; d < 3; ++d) g->met_ff.idcf[d] = (const float2*)g->met_fn.idc[d];
+  }
+  FV_TRY(alloc(g, (void**)&g->Uff, g->nvel * sizeof(float2)));
+  FV_TRY(alloc(g, (void**)&g->xff, g->nvel * sizeof(float2)));
   FV_TRY(alloc(g, (void**)&g->d_scal, kScalars * sizeof(double)));
   g->part_len = 4096 * 130;
   FV_TRY(alloc(g, (void**)&g->d_part, g->part_len * sizeof(double)));
@@ -412,7 +448,8 @@ void fv_grid_destroy(fv_grid* g) {
   void* ptrs[] = {g->d_met_d, g->d_met_f, g->d_tpf_d, g->d_tpf_f, g->vel_buf[0], g->vel_buf[1],
                   g->vel_buf[2], g->cell_buf[0], g->cell_buf[1], g->cell_buf[2], g->tpf_buf[0],
                   g->tpf_buf[1], g->d_scal, g->d_part, g->kry, g->kry_small, g->U32, g->x32,
-                  g->w32, g->vff[0], g->vff[1], g->pff, g->r32, g->phi32, g->d_met_ff};
+                  g->w32, g->vff[0], g->vff[1], g->pff, g->r32, g->phi32, g->d_met_ff,
+                  g->d_met_fn, g->Uff, g->xff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_scal) cudaFreeHost(g->h_scal);

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "fvns.h"
+#include "fv_ff.cuh"
 
 namespace fv {
 
@@ -63,6 +64,7 @@ struct MetFF {
   int64_t ncell;
   const float* idc[3];
   const float2* idx[3];
+  const float2* idcf[3];   // float-float 1/dc (gradient of the FV_FF loop)
 };
 
 template <typename T>
@@ -86,6 +88,7 @@ struct LoopState {
 struct GraphCache {
   bool ready = false;
   double sigma = 0.0;
+  int prec = FV_MIXED;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t init_node = nullptr;
@@ -136,9 +139,14 @@ struct fv_grid {
   float* phi32 = nullptr;        // n_cell
   void* d_met_ff = nullptr;      // float-float 1/dx per axis
   fv::MetFF met_ff;
+  // float-float metrics and operands of the FV_FF J.v
+  void* d_met_fn = nullptr;
+  fv::Met<fv::ffn> met_fn;
+  float2* Uff = nullptr;         // n_vel
+  float2* xff = nullptr;         // n_vel
 
   // captured evaluation graphs of the mixed path (built on first use)
-  fv::GraphCache graphs[2];
+  fv::GraphCache graphs[4];
   mutable bool capturing = false;
   bool use_graph = true;          // FVNS_NO_GRAPH=1 selects the host-driven loop
 
@@ -211,19 +219,25 @@ fv_status launch_round_f32(const fv_grid* g, const double* in, float* out, int64
 fv_status launch_div_f32(const fv_grid* g, const float* w32, float* r32);
 // one float-float SIMPLE pass; first: vin is the float32 w, p starts at 0
 fv_status launch_correct_ff(const fv_grid* g, bool first, const void* vin, float2* vout,
-                            const float* phi, float2* p, float* r, double omega);
+                            const float* phi, float2* p, float* r, double omega, bool ffg = false);
 // out = hi + lo (- sigma * x) as float64; p_out = p_ff
 fv_status launch_join_ff(const fv_grid* g, const float2* v, const double* x, double sigma,
                          double* out, int64_t n);
 fv_status launch_join_ff_cells(const fv_grid* g, const float2* p, double* out);
 fv_status launch_widen_f32(const fv_grid* g, const float* in, double* out, int64_t n);
 
+// FV_FF operands and stencil (fv_mixed.cu)
+fv_status launch_split_ff(const fv_grid* g, const double* in, float2* out, int64_t n);
+fv_status launch_momentum_ff(const fv_grid* g, const float2* U, const float2* v, float2* out,
+                             double shift);
+fv_status launch_div_ff(const fv_grid* g, const float2* w, float* r32);
+
 // graph path (fv_graph.cu): one mixed-precision Krylov-vector evaluation as
 // one graph launch; with sync, the loop statistics are read back.
 fv_status mixed_krylov_graph(const fv_grid* g, const double* U, const double* x, double* out,
                              double* p, double sigma, double eps, int max_pass, double omega,
                              bool sync, int* passes, double* phi1, double* phil, double* divl,
-                             int* status);
+                             int* status, int prec = FV_MIXED);
 void destroy_graph_cache(GraphCache& c);
 
 // tensor-product pressure solve: phi = (D G)^+ r ; phi is float or double

@@ -326,10 +326,12 @@ static float slot_float(const double* h, int slot) {
 // out = v - sigma x (float64) and p_out (optional).
 static fv_status simple_loop_ff(const fv_grid* g, double* out, double* p_out, const double* x,
                                 double sigma, double eps, int max_pass, double omega,
-                                SimpleResult* res_out) {
+                                SimpleResult* res_out, bool ff_start = false) {
   SimpleResult local;
   SimpleResult* res = res_out ? res_out : &local;
-  const void* cur = g->w32;
+  // ff_start: the predictor is the float-float field in vff[1] and p starts at 0
+  const void* cur = ff_start ? (const void*)g->vff[1] : (const void*)g->w32;
+  if (ff_start) FV_CUDA(cudaMemsetAsync(g->pff, 0, g->ncell * sizeof(float2), g->stream));
   int nxt = 0;
   double h[kScalars];
   double phi1 = 0.0;
@@ -339,7 +341,8 @@ static fv_status simple_loop_ff(const fv_grid* g, double* out, double* p_out, co
   for (int pass = 1; pass <= max_pass; ++pass) {
     FV_TRY(tpf_solve_f32(g, g->r32, g->phi32));
     FV_TRY(reset_scalars(g));
-    FV_TRY(launch_correct_ff(g, pass == 1, cur, g->vff[nxt], g->phi32, g->pff, g->r32, omega));
+    FV_TRY(launch_correct_ff(g, pass == 1 && !ff_start, cur, g->vff[nxt], g->phi32, g->pff, g->r32,
+                             omega, ff_start));
     cur = g->vff[nxt];
     nxt ^= 1;
     FV_TRY(fetch_scalars(g, h));
@@ -365,16 +368,23 @@ static fv_status simple_loop_ff(const fv_grid* g, double* out, double* p_out, co
 static fv_status krylov_apply(const fv_grid* g, const double* U, const double* x, double* out,
                               double* p, double sigma, int prec, double eps, int max_pass,
                               double omega, SimpleResult* res) {
-  if (prec == FV_MIXED) {
+  if (prec == FV_MIXED || prec == FV_FF) {
     if (g->use_graph) {
       int status = 0;
       FV_TRY(mixed_krylov_graph(g, U, x, out, p, sigma, eps, max_pass, omega, res != nullptr,
                                 res ? &res->passes : nullptr, res ? &res->phi_first : nullptr,
                                 res ? &res->phi_last : nullptr, res ? &res->div_max : nullptr,
-                                &status));
+                                &status, prec));
       if (res && status == 3) { set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN; }
       if (res && status == 2) { set_error("SIMPLE loop reached max_pass"); return FV_ENOCONV; }
       return FV_OK;
+    }
+    if (prec == FV_FF) {
+      FV_TRY(launch_split_ff(g, U, g->Uff, g->nvel));
+      FV_TRY(launch_split_ff(g, x, g->xff, g->nvel));
+      FV_TRY(launch_momentum_ff(g, g->Uff, g->xff, g->vff[1], sigma));
+      FV_TRY(launch_div_ff(g, g->vff[1], g->r32));
+      return simple_loop_ff(g, out, p, x, sigma, eps, max_pass, omega, res, true);
     }
     FV_TRY(launch_round_f32(g, U, g->U32, g->nvel));
     FV_TRY(launch_round_f32(g, x, g->x32, g->nvel));
@@ -479,8 +489,14 @@ fv_status ns_residual(const fv_grid* g, const double* U, const double* P, double
 fv_status ns_jacvec(const fv_grid* g, const double* U, const double* v, double* Jv, int prec) {
   FV_TRY(check_grid(g, "ns_jacvec"));
   if (!U || !v || !Jv) { set_error("ns_jacvec: NULL pointer"); return FV_EINVAL; }
-  if (prec != FV_FP64 && prec != FV_MIXED) { set_error("ns_jacvec: bad prec"); return FV_EINVAL; }
+  if (prec != FV_FP64 && prec != FV_MIXED && prec != FV_FF) { set_error("ns_jacvec: bad prec"); return FV_EINVAL; }
   if (v == Jv || U == Jv) { set_error("ns_jacvec: output aliases an input"); return FV_EINVAL; }
+  if (prec == FV_FF) {
+    FV_TRY(launch_split_ff(g, U, g->Uff, g->nvel));
+    FV_TRY(launch_split_ff(g, v, g->xff, g->nvel));
+    FV_TRY(launch_momentum_ff(g, g->Uff, g->xff, g->vff[1], 0.0));
+    return launch_join_ff(g, g->vff[1], nullptr, 0.0, Jv, g->nvel);
+  }
   return launch_momentum_jac(g, U, v, Jv, prec, 0.0);
 }
 
@@ -500,12 +516,12 @@ fv_status simple_krylov_solve(const fv_grid* g, const double* U, const double* v
   if (o.eps <= 0.0) o.eps = 1e-8;
   if (o.max_pass <= 0) o.max_pass = 200;
   if (o.omega <= 0.0) o.omega = 1.0;
-  if (o.omega > 1.0 || (o.prec != FV_FP64 && o.prec != FV_MIXED) || o.sigma < 0.0) {
+  if (o.omega > 1.0 || (o.prec != FV_FP64 && o.prec != FV_MIXED && o.prec != FV_FF) || o.sigma < 0.0) {
     set_error("simple_krylov_solve: bad option");
     return FV_EINVAL;
   }
   SimpleResult r;
-  const bool no_sync = o.async != 0 && o.prec == FV_MIXED;
+  const bool no_sync = o.async != 0 && o.prec != FV_FP64;
   fv_status s = krylov_apply(g, U, v_in, v_out, p_out, o.sigma, o.prec, o.eps, o.max_pass, o.omega,
                              no_sync ? nullptr : &r);
   if (stats && !no_sync) {
@@ -531,7 +547,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
   if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-8;
   if (o.sigma <= 0) o.sigma = 10.0;
   if (o.simple_eps <= 0) o.simple_eps = 1e-10;
-  if (o.gmres_m > kMaxVec - 2 || (o.prec != FV_FP64 && o.prec != FV_MIXED)) {
+  if (o.gmres_m > kMaxVec - 2 || (o.prec != FV_FP64 && o.prec != FV_MIXED && o.prec != FV_FF)) {
     set_error("newton_steady: bad option (gmres_m <= 128, prec)");
     return FV_EINVAL;
   }
@@ -675,7 +691,7 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
   if (o.max_restarts <= 0) o.max_restarts = 5000;
   if (o.sigma <= 0) o.sigma = 10.0;
   if (o.simple_eps <= 0) o.simple_eps = 1e-10;
-  if (o.prec != FV_FP64 && o.prec != FV_MIXED) { set_error("arnoldi_leading: bad prec"); return FV_EINVAL; }
+  if (o.prec != FV_FP64 && o.prec != FV_MIXED && o.prec != FV_FF) { set_error("arnoldi_leading: bad prec"); return FV_EINVAL; }
   FV_TRY(ensure_krylov(g, m + 1));
   const int64_t nv = g->nvel;
   double* V = g->kry;

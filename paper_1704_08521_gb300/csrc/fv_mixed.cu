@@ -11,6 +11,7 @@
 // are fused in one kernel (ping-pong buffers, no read-after-write hazard).
 #include "fv_ff.cuh"
 #include "fv_internal.cuh"
+#include "fv_stencil_dev.cuh"
 
 namespace fv {
 
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(256) k_div_f32(MetFF m, const float* __restric
 // One pass: v_out = v_in - omega G phi (own faces), p += omega phi, and
 // r = D v_out in float-float arithmetic, rounded to float32 for the next
 // pressure-correction solve.  FIRST: v_in is the float32 predictor w.
-template <bool FIRST>
+template <bool FIRST, bool FFG = false>
 __global__ void __launch_bounds__(256) k_correct_ff(MetFF m, const void* __restrict__ vin_,
                                                     float2* __restrict__ vout,
                                                     const float* __restrict__ phi,
@@ -105,13 +106,23 @@ __global__ void __launch_bounds__(256) k_correct_ff(MetFF m, const void* __restr
       const int q = pos[c];
       ff lo = {0.f, 0.f}, hi = {0.f, 0.f};
       if (q > 0) {
-        const float g = (f0 - __ldg(phi + base - st[c])) * m.idc[c][q];
-        lo = ff_add_f(load(c * nc + base), -omega * g);
+        if (FFG) {   // gradient of the float32 phi evaluated in float-float
+          const ff gr = ff_mul(two_sum(f0, -__ldg(phi + base - st[c])), of2(m.idcf[c][q]));
+          lo = ff_sub(load(c * nc + base), ff_mul_f(gr, omega));
+        } else {
+          const float g = (f0 - __ldg(phi + base - st[c])) * m.idc[c][q];
+          lo = ff_add_f(load(c * nc + base), -omega * g);
+        }
       }
       vout[c * nc + base] = to2(lo);
       if (q + 1 < m.n[c]) {
-        const float g = (__ldg(phi + base + st[c]) - f0) * m.idc[c][q + 1];
-        hi = ff_add_f(load(c * nc + base + st[c]), -omega * g);
+        if (FFG) {
+          const ff gr = ff_mul(two_sum(__ldg(phi + base + st[c]), -f0), of2(m.idcf[c][q + 1]));
+          hi = ff_sub(load(c * nc + base + st[c]), ff_mul_f(gr, omega));
+        } else {
+          const float g = (__ldg(phi + base + st[c]) - f0) * m.idc[c][q + 1];
+          hi = ff_add_f(load(c * nc + base + st[c]), -omega * g);
+        }
       }
       dv = ff_add(dv, ff_mul(ff_sub(hi, lo), of2(m.idx[c][q])));
     }
@@ -137,6 +148,67 @@ __global__ void k_join_ff(const float2* __restrict__ v, const double* __restrict
     ff a = of2(__ldg(v + e));
     if (x) a = ff_sub(a, ff_mul_f(f64_split(__ldg(x + e)), sigma));
     out[e] = ff_join(a.hi, a.lo);
+  }
+}
+
+// FV_FF operands: exact float-float split of float64 values
+__global__ void k_split_ff(const double* __restrict__ in, float2* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = to2(f64_split(__ldg(in + e)));
+}
+
+// J.v (Eq. 10) in float-float arithmetic: same stencil template as the
+// float32 / float64 kernels, instantiated with the float-float number type
+// (this file is compiled without FMA contraction, so every TwoSum and
+// TwoProd keeps its rounding)
+__global__ void __launch_bounds__(256) k_momentum_ff(Met<ffn> m, const float2* __restrict__ U,
+                                                     const float2* __restrict__ V,
+                                                     float2* __restrict__ out, ffn inv_re,
+                                                     ffn shift) {
+  const int plane_ = m.n[0] * m.n[1];
+  const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t_ >= plane_) return;
+  const int i = t_ % m.n[0], j = t_ / m.n[0];
+  const int st[3] = {1, m.n[0], plane_};
+  const int nc = (int)m.ncell;
+  for (int kk = 0; kk < kCellKz; ++kk) {
+    const int k = blockIdx.y * kCellKz + kk;
+    if (k >= m.n[2]) return;
+    const int pos[3] = {i, j, k};
+    const int base = k * plane_ + t_;
+    ffn r0, r1, r2;
+    if (i > 0) r0 = stencil::momentum_face<ffn, 0, true, float2>(m, U, V, base, pos, st, inv_re, ffn(0), shift);
+    if (j > 0) r1 = stencil::momentum_face<ffn, 1, true, float2>(m, U, V, base, pos, st, inv_re, ffn(0), shift);
+    if (k > 0) r2 = stencil::momentum_face<ffn, 2, true, float2>(m, U, V, base, pos, st, inv_re, ffn(0), shift);
+    out[base] = make_float2(r0.hi, r0.lo);
+    out[nc + base] = make_float2(r1.hi, r1.lo);
+    out[2 * nc + base] = make_float2(r2.hi, r2.lo);
+  }
+}
+
+// D w of a float-float field, rounded to float32 (first pressure rhs of FV_FF)
+__global__ void __launch_bounds__(256) k_div_ff(MetFF m, const float2* __restrict__ w,
+                                                float* __restrict__ r) {
+  const int plane_ = m.n[0] * m.n[1];
+  const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t_ >= plane_) return;
+  const int i = t_ % m.n[0], j = t_ / m.n[0];
+  const int nx = m.n[0], ny = m.n[1], nz = m.n[2];
+  const int nc = (int)m.ncell;
+  for (int kk = 0; kk < kCellKz; ++kk) {
+    const int k = blockIdx.y * kCellKz + kk;
+    if (k >= nz) return;
+    const int base = k * plane_ + t_;
+    const ff z = {0.f, 0.f};
+    const ff u0 = (i > 0) ? of2(w[base]) : z, u1 = (i + 1 < nx) ? of2(w[base + 1]) : z;
+    const ff v0 = (j > 0) ? of2(w[nc + base]) : z, v1 = (j + 1 < ny) ? of2(w[nc + base + nx]) : z;
+    const ff w0 = (k > 0) ? of2(w[2 * nc + base]) : z;
+    const ff w1 = (k + 1 < nz) ? of2(w[2 * nc + base + plane_]) : z;
+    ff d = ff_mul(ff_sub(u1, u0), of2(m.idx[0][i]));
+    d = ff_add(d, ff_mul(ff_sub(v1, v0), of2(m.idx[1][j])));
+    d = ff_add(d, ff_mul(ff_sub(w1, w0), of2(m.idx[2][k])));
+    r[base] = d.hi;
   }
 }
 
@@ -181,13 +253,16 @@ fv_status launch_div_f32(const fv_grid* g, const float* w32, float* r32) {
 }
 
 fv_status launch_correct_ff(const fv_grid* g, bool first, const void* vin, float2* vout,
-                            const float* phi, float2* p, float* r, double omega) {
+                            const float* phi, float2* p, float* r, double omega, bool ffg) {
   const int bx = block_x(g);
   {
     LaunchScope ls_(g, FV_K_CORRECT);
     if (first)
       k_correct_ff<true><<<cell_grid(g, bx), bx, 0, g->stream>>>(g->met_ff, vin, vout, phi, p, r,
                                                                  float(omega), g->d_scal);
+    else if (ffg)
+      k_correct_ff<false, true><<<cell_grid(g, bx), bx, 0, g->stream>>>(g->met_ff, vin, vout, phi, p,
+                                                                        r, float(omega), g->d_scal);
     else
       k_correct_ff<false><<<cell_grid(g, bx), bx, 0, g->stream>>>(g->met_ff, vin, vout, phi, p, r,
                                                                   float(omega), g->d_scal);
@@ -201,6 +276,36 @@ fv_status launch_join_ff(const fv_grid* g, const float2* v, const double* x, dou
   {
     LaunchScope ls_(g, FV_K_VECTOR);
     k_join_ff<<<grid1d(n), 256, 0, g->stream>>>(v, x, float(sigma), out, n);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_split_ff(const fv_grid* g, const double* in, float2* out, int64_t n) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_split_ff<<<grid1d(n), 256, 0, g->stream>>>(in, out, n);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_momentum_ff(const fv_grid* g, const float2* U, const float2* v, float2* out,
+                             double shift) {
+  const ff ir = f64_split(1.0 / g->re), sh = f64_split(shift);
+  {
+    LaunchScope ls_(g, FV_K_MOMENTUM);
+    k_momentum_ff<<<cell_grid(g, 0), kCellThreads, 0, g->stream>>>(
+        g->met_fn, U, v, out, ffn(ir), ffn(sh));
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_div_ff(const fv_grid* g, const float2* w, float* r32) {
+  {
+    LaunchScope ls_(g, FV_K_DIVERGENCE);
+    k_div_ff<<<cell_grid(g, 0), kCellThreads, 0, g->stream>>>(g->met_ff, w, r32);
   }
   FV_CHECK_LAUNCH();
   return FV_OK;

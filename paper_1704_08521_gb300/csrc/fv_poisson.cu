@@ -607,7 +607,7 @@ using namespace fv;
 
 extern "C" fv_status fv_pressure_solve(const fv_grid* g, const double* r, double* phi, int prec) {
   if (!g || !r || !phi) { set_error("fv_pressure_solve: NULL argument"); return FV_EINVAL; }
-  if (prec != FV_FP64 && prec != FV_MIXED) { set_error("fv_pressure_solve: bad prec"); return FV_EINVAL; }
+  if (prec != FV_FP64 && prec != FV_MIXED && prec != FV_FF) { set_error("fv_pressure_solve: bad prec"); return FV_EINVAL; }
   if (prec == FV_FP64) return tpf_solve(g, r, phi, FV_FP64);
   // mixed: float32 solve, widened into phi
   FV_TRY(launch_round_f32(g, r, g->r32, g->ncell));

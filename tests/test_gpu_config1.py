@@ -51,13 +51,14 @@ def test_config1_newton_matches_oracle(fv, prec):
     assert hist[-1][2] < 1e-10
 
 
-def test_config1_arnoldi_matches_oracle(fv):
+@pytest.mark.parametrize("prec", ["fp64", "ff"])
+def test_config1_arnoldi_matches_oracle(fv, prec):
     gold = np.load(GOLD)
     g = fv.Grid(N, N, N, "cosine", alpha=0.0, re=1000.0)
     U = torch.tensor(gold["U"], device="cuda")
     v0 = torch.tensor(synth.gaussian_velocity((N, N, N), 1), device="cuda")
     evec = torch.empty(2 * g.n_vel, dtype=torch.float64, device="cuda")
-    lam, info = fv.arnoldi_leading(g, U, v0, m=30, nev=5, evec=evec, prec="fp64")
+    lam, info = fv.arnoldi_leading(g, U, v0, m=30, nev=5, evec=evec, prec=prec)
     lam = np.array(lam)
     ref = gold["lam"]
     for l in lam:                   # as sets: conjugate ordering may differ

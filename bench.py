@@ -226,6 +226,34 @@ def run_ours(args):
         barrier()
         fp64 = k64 / (e0.elapsed_time(e1) / 1e3)
 
+    # the float-float form (FP64-level accuracy on the FP32 pipes), a few steps
+    ff_rate = None
+    if mixed:
+        kff = max(3, min(args.steps, 10))
+        step(0, "ff", async_=False)
+        barrier()
+        e0.record(stream)
+        for s in range(kff):
+            step(s, "ff", async_=True)
+        e1.record(stream)
+        barrier()
+        ff_rate = kff / (e0.elapsed_time(e1) / 1e3)
+
+    # one Arnoldi cycle (Krylov dimension 60: 60 Krylov vectors + CGS2 in the
+    # W-inner product + the Hessenberg step) on this base flow: time per
+    # Arnoldi iteration, the unit the paper's eigenvalue times are made of
+    arnoldi_ms = {}
+    if mixed:
+        for prec in ("mixed", "ff"):
+            barrier()
+            t0 = time.perf_counter()
+            try:
+                fv.arnoldi_leading(g, U, V[0], m=60, nev=10, max_restarts=1, prec=prec)
+            except fv.FvError:
+                pass                      # one cycle is not enough to converge
+            torch.cuda.synchronize()
+            arnoldi_ms[prec] = 1e3 * (time.perf_counter() - t0) / 60
+
     # per-kernel device time: back-to-back launches of each kernel class on
     # the grid's stream, timed with CUDA events (fv_bench_kernel)
     prof = {}
@@ -310,6 +338,8 @@ def run_ours(args):
         "sweeps_per_s": value * passes,
         "mcell_jv_per_s": None,
         "fp64_form_solves_per_s": fp64,
+        "ff_form_solves_per_s": ff_rate,
+        "arnoldi_iteration_ms": arnoldi_ms,
         "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": gpu_launches,
         "kernels_per_solve": kernels_per_solve,

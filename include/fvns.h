@@ -244,6 +244,72 @@ fv_status fv_batch_autotune(fv_batch* b, int* best, double* ms);
 /* Set the z-planes per work item explicitly (e.g. from a cached tuning). */
 fv_status fv_batch_set_tile(fv_batch* b, int planes);
 
+/* Section 3 step 1, right-hand side: r[n_cell] = D v, the finite-volume
+ * divergence of v[n_vel] (outflux of each cell over its volume; the wall
+ * faces carry zero normal velocity).  float64, device. */
+fv_status ns_divergence(const fv_grid* g, const double* v, double* r);
+
+/* ------------------------------------------------------- learned guess --
+ * Optional first pass of the SIMPLE-like loop of Section 3 from a learned
+ * guess of the pressure correction.  The paper has no counterpart: the
+ * paper's loop starts every evaluation from phi = 0 and an exact solve.
+ * A 3-D convolutional U-Net (4 levels of 16/32/48/64 channels, two 3x3x3
+ * convolutions + ReLU per level, 2x2x2 mean pooling, nearest upsampling
+ * with skip concatenation, a 1x1x1 output layer; BF16 weights and
+ * activations, float32 accumulation on the tensor cores) maps the
+ * right-hand side in index units, q = r (dx_i dy_j dz_k)^(2/3) with
+ * r = D w, scaled by 1/S (S = rms of q), and the metric channels
+ * log(n_x dx_i), log(n_y dy_j), log(n_z dz_k) to phi / S.  Grid
+ * dimensions: multiples of 8 in [8, 1024].  The network owns its parameters (float32 + BF16 mirror, Adam
+ * moments) and an activation workspace that grows to the largest grid it
+ * has seen.  Parameter layout (float32): for each of the 14 convolutions,
+ * in order encoder 0a, 0b, 1a, 1b, 2a, 2b, bottom a, b, decoder 2a, 2b, 1a,
+ * 1b, 0a, 0b, the weights W[27][cout][cin] (tap 9(dz+1)+3(dy+1)+(dx+1))
+ * then the bias[cout]; last the 16 output weights and the output bias.
+ * Channels (cin -> cout): 16->16, 16->16, 16->32, 32->32, 32->48, 48->48,
+ * 48->64, 64->64, 112->48, 48->48, 80->32, 32->32, 48->16, 16->16; decoder
+ * inputs are [upsampled coarser output, skip of the same level].  The
+ * network input has 16 channels: the 4 above, then 12 zeros. */
+typedef struct fv_unet fv_unet;
+/* He-normal weights from seed, zero biases; work on cuda_stream. */
+fv_status fv_unet_create(uint64_t seed, void* cuda_stream, fv_unet** out);
+void fv_unet_destroy(fv_unet* u);
+int fv_unet_param_count(const fv_unet* u);
+fv_status fv_unet_set_stream(fv_unet* u, void* cuda_stream);
+/* Copy all parameters in (device, float32, param_count); resets Adam. */
+fv_status fv_unet_set_params(fv_unet* u, const float* params);
+/* Copy parameters and/or the gradients of the last backward pass out
+ * (device, float32, param_count; either may be NULL). */
+fv_status fv_unet_get_params(const fv_unet* u, float* params, float* grads);
+/* Raw forward pass: in[4][n_cell] (device float32 input planes, cells x
+ * fastest), out[n_cell] (device float32). */
+fv_status fv_unet_forward(fv_unet* u, int nx, int ny, int nz, const float* in, float* out);
+/* Gradients of the mean-free square loss L = mean((e - mean e)^2),
+ * e = out - target (target: device float32, n_cell), with respect to every
+ * parameter, for the last forward pass.  *loss (host, optional) = L; the
+ * call then synchronises the network's stream. */
+fv_status fv_unet_backward(fv_unet* u, const float* target, double* loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with the last gradients. */
+fv_status fv_unet_adam(fv_unet* u, float lr);
+/* phi[n_cell] (device float64) = the network's guess for the Poisson
+ * right-hand side r[n_cell] (device float64) on grid g (g's stream). */
+fv_status fv_unet_guess(fv_unet* u, const fv_grid* g, const double* r, double* phi);
+/* One training step on the pair (r, phi) of grid g: normalise, forward,
+ * backward, Adam; *loss (host, optional) = the loss before the step. */
+fv_status fv_unet_train_step(fv_unet* u, const fv_grid* g, const double* r, const double* phi,
+                             float lr, double* loss);
+/* simple_krylov_solve (prec FV_MIXED or FV_FF, host-driven loop) whose
+ * first pass takes phi from the network instead of the exact solve; the
+ * following passes are the exact tensor-product solves of the paper's loop.
+ * The stop test keeps the tolerance of the plain loop: corrections are
+ * compared with the pressure after the first exact pass (guess + its
+ * correction), the plain loop's first correction.  stats->passes counts
+ * the guess pass; a net whose guess does not converge under the same test
+ * returns FV_ENOCONV like the plain loop. */
+fv_status simple_krylov_solve_guess(const fv_grid* g, fv_unet* u, const double* U,
+                                    const double* v_in, double* v_out, double* p_out,
+                                    const fv_simple_opts* opts, fv_simple_stats* stats);
+
 /* W-weighted inner product <a, b> = sum over velocity faces of the momentum
  * control-volume size times a b (wall faces excluded).  Result to host. */
 fv_status fv_dot_w(const fv_grid* g, const double* a, const double* b, double* out /* host */);

@@ -308,3 +308,91 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def ns_divergence(g, v, r):
+    """r = D v (Section 3 step 1), float64 device tensors."""
+    check(lib.ns_divergence(g.handle, _f64(v, g.n_vel, "v"), _f64(r, g.n_cell, "r")),
+          "ns_divergence")
+
+
+def _f32(t, n, name):
+    import torch
+    if t.dtype != torch.float32 or t.numel() != n:
+        raise ValueError(f"{name}: expected {n} float32 values, got {t.numel()} {t.dtype}")
+    return _ptr(t)
+
+
+class UNet:
+    """Owner of an fv_unet handle: the learned guess of the pressure
+    correction (3-D conv U-Net, BF16 tensor-core kernels)."""
+
+    def __init__(self, seed=0, stream=None):
+        h = ctypes.c_void_p()
+        st = _stream() if stream is None else ctypes.c_void_p(stream)
+        check(lib.fv_unet_create(seed, st, ctypes.byref(h)), "fv_unet_create")
+        self.handle = h
+        self.n_param = lib.fv_unet_param_count(h)
+
+    def set_stream(self, stream):
+        check(lib.fv_unet_set_stream(self.handle, ctypes.c_void_p(stream)), "fv_unet_set_stream")
+
+    def set_params(self, params):
+        check(lib.fv_unet_set_params(self.handle, _f32(params, self.n_param, "params")),
+              "fv_unet_set_params")
+
+    def get_params(self, params=None, grads=None):
+        check(lib.fv_unet_get_params(
+            self.handle, None if params is None else _f32(params, self.n_param, "params"),
+            None if grads is None else _f32(grads, self.n_param, "grads")), "fv_unet_get_params")
+
+    def forward(self, shape, planes, out):
+        nx, ny, nz = shape
+        n = nx * ny * nz
+        check(lib.fv_unet_forward(self.handle, nx, ny, nz, _f32(planes, 4 * n, "planes"),
+                                  _f32(out, n, "out")), "fv_unet_forward")
+
+    def backward(self, target):
+        loss = ctypes.c_double()
+        check(lib.fv_unet_backward(self.handle, _f32(target, target.numel(), "target"),
+                                   ctypes.byref(loss)), "fv_unet_backward")
+        return loss.value
+
+    def adam(self, lr):
+        check(lib.fv_unet_adam(self.handle, lr), "fv_unet_adam")
+
+    def guess(self, g, r, phi):
+        check(lib.fv_unet_guess(self.handle, g.handle, _f64(r, g.n_cell, "r"),
+                                _f64(phi, g.n_cell, "phi")), "fv_unet_guess")
+
+    def train_step(self, g, r, phi, lr):
+        loss = ctypes.c_double()
+        check(lib.fv_unet_train_step(self.handle, g.handle, _f64(r, g.n_cell, "r"),
+                                     _f64(phi, g.n_cell, "phi"), lr, ctypes.byref(loss)),
+              "fv_unet_train_step")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.fv_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simple_krylov_solve_guess(g, net, U, v_in, v_out, p_out=None, eps=1e-8, max_pass=200,
+                              prec="mixed", omega=1.0, sigma=0.0):
+    """simple_krylov_solve whose first pass takes phi from the network."""
+    o = fv_simple_opts(eps, max_pass, PRECS.get(prec, prec), omega, sigma, 0)
+    s = fv_simple_stats()
+    check(lib.simple_krylov_solve_guess(g.handle, net.handle, _f64(U, g.n_vel, "U"),
+                                        _f64(v_in, g.n_vel, "v_in"), _f64(v_out, g.n_vel, "v_out"),
+                                        None if p_out is None else _f64(p_out, g.n_cell, "p_out"),
+                                        ctypes.byref(o), ctypes.byref(s)),
+          "simple_krylov_solve_guess")
+    return {"passes": s.passes, "phi_first": s.phi_first, "phi_last": s.phi_last,
+            "div_max": s.div_max}

@@ -41,6 +41,19 @@ _SIGS = {
     "newton_steady": (_I, [_P, _P, _P, _P, _P]),
     "arnoldi_leading": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P]),
     "fv_dot_w": (_I, [_P, _P, _P, _P]),
+    "ns_divergence": (_I, [_P, _P, _P]),
+    "fv_unet_create": (_I, [ctypes.c_uint64, _P, ctypes.POINTER(_P)]),
+    "fv_unet_destroy": (None, [_P]),
+    "fv_unet_param_count": (_I, [_P]),
+    "fv_unet_set_stream": (_I, [_P, _P]),
+    "fv_unet_set_params": (_I, [_P, _P]),
+    "fv_unet_get_params": (_I, [_P, _P, _P]),
+    "fv_unet_forward": (_I, [_P, _I, _I, _I, _P, _P]),
+    "fv_unet_backward": (_I, [_P, _P, ctypes.POINTER(_D)]),
+    "fv_unet_adam": (_I, [_P, ctypes.c_float]),
+    "fv_unet_guess": (_I, [_P, _P, _P, _P]),
+    "fv_unet_train_step": (_I, [_P, _P, _P, _P, ctypes.c_float, ctypes.POINTER(_D)]),
+    "simple_krylov_solve_guess": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "fv_batch_create": (_I, [_I, _P, _P, ctypes.POINTER(_P)]),
     "fv_batch_destroy": (None, [_P]),
     "fv_batch_krylov": (_I, [_P, _P, _P, _P, _D, _D, _P]),

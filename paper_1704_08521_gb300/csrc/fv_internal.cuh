@@ -243,6 +243,10 @@ void destroy_graph_cache(GraphCache& c);
 // tensor-product pressure solve: phi = (D G)^+ r ; phi is float or double
 fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec);
 fv_status tpf_solve_f32(const fv_grid* g, const float* r, float* phi);
+// learned first pass of the SIMPLE loop (fv_unet.cu): phi = guess for r
+fv_status unet_guess_f32(fv_unet* u, const fv_grid* g, const float* r, float* phi);
+// max |x[0..n)| of a float32 array to the host (synchronises g's stream)
+fv_status absmax_f32_host(const fv_grid* g, const float* x, int64_t n, double* out);
 fv_status tpf_one_transform_f32(const fv_grid* g, int axis);
 
 // vector kernels (weighted inner products, Gram-Schmidt)

@@ -324,9 +324,13 @@ static float slot_float(const double* h, int slot) {
 // Mixed-precision SIMPLE loop on the float-float state, starting from the
 // float32 predictor in g->w32 whose divergence is in g->r32.  Writes
 // out = v - sigma x (float64) and p_out (optional).
+// phi_guess (optional): pass 1 takes this float32 phi instead of the exact
+// solve; the stop test then refers to max |p| after pass 2 (guess + first
+// exact correction), the first exact correction of the plain loop.
 static fv_status simple_loop_ff(const fv_grid* g, double* out, double* p_out, const double* x,
                                 double sigma, double eps, int max_pass, double omega,
-                                SimpleResult* res_out, bool ff_start = false) {
+                                SimpleResult* res_out, bool ff_start = false,
+                                const float* phi_guess = nullptr) {
   SimpleResult local;
   SimpleResult* res = res_out ? res_out : &local;
   // ff_start: the predictor is the float-float field in vff[1] and p starts at 0
@@ -338,10 +342,13 @@ static fv_status simple_loop_ff(const fv_grid* g, double* out, double* p_out, co
   res->passes = 0;
   res->phi_last = 0.0;
   fv_status st = FV_ENOCONV;
+  const int first_exact = phi_guess ? 2 : 1;
   for (int pass = 1; pass <= max_pass; ++pass) {
-    FV_TRY(tpf_solve_f32(g, g->r32, g->phi32));
+    const float* phi = g->phi32;
+    if (pass == 1 && phi_guess) phi = phi_guess;
+    else FV_TRY(tpf_solve_f32(g, g->r32, g->phi32));
     FV_TRY(reset_scalars(g));
-    FV_TRY(launch_correct_ff(g, pass == 1 && !ff_start, cur, g->vff[nxt], g->phi32, g->pff, g->r32,
+    FV_TRY(launch_correct_ff(g, pass == 1 && !ff_start, cur, g->vff[nxt], phi, g->pff, g->r32,
                              omega, ff_start));
     cur = g->vff[nxt];
     nxt ^= 1;
@@ -350,12 +357,16 @@ static fv_status simple_loop_ff(const fv_grid* g, double* out, double* p_out, co
     if (h[S_NAN] != 0.0) { set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN; }
     const double ph = slot_float(h, S_PHI_MAX_F);
     res->div_max = slot_float(h, S_DIV_MAX_F);
-    if (pass == 1) phi1 = ph;
-    res->phi_first = phi1;
     const double prev = res->phi_last;
     res->phi_last = ph;
+    if (pass < first_exact) continue;   // the guess pass never ends the loop
+    if (pass == first_exact) {
+      phi1 = ph;
+      if (phi_guess) FV_TRY(absmax_f32_host(g, (const float*)g->pff, 2 * g->ncell, &phi1));
+    }
+    res->phi_first = phi1;
     if (ph == 0.0 || ph <= eps * phi1) { st = FV_OK; break; }
-    if (pass >= 3 && ph > 0.25 * prev && ph <= 1e-9 * phi1) { st = FV_OK; break; }
+    if (pass >= first_exact + 2 && ph > 0.25 * prev && ph <= 1e-9 * phi1) { st = FV_OK; break; }
   }
   FV_TRY(launch_join_ff(g, (const float2*)cur, sigma != 0.0 ? x : nullptr, sigma, out, g->nvel));
   if (p_out) FV_TRY(launch_join_ff_cells(g, g->pff, p_out));
@@ -531,6 +542,54 @@ fv_status simple_krylov_solve(const fv_grid* g, const double* U, const double* v
     stats->div_max = r.div_max;
   }
   return s;
+}
+
+fv_status simple_krylov_solve_guess(const fv_grid* g, fv_unet* u, const double* U,
+                                    const double* v_in, double* v_out, double* p_out,
+                                    const fv_simple_opts* opts, fv_simple_stats* stats) {
+  FV_TRY(check_grid(g, "simple_krylov_solve_guess"));
+  if (!u || !U || !v_in || !v_out) { set_error("simple_krylov_solve_guess: NULL pointer"); return FV_EINVAL; }
+  if (v_in == v_out) { set_error("simple_krylov_solve_guess: v_in and v_out alias"); return FV_EINVAL; }
+  fv_simple_opts o = {};
+  if (opts) o = *opts;
+  if (o.eps <= 0.0) o.eps = 1e-8;
+  if (o.max_pass <= 0) o.max_pass = 200;
+  if (o.omega <= 0.0) o.omega = 1.0;
+  if (o.omega > 1.0 || (o.prec != FV_MIXED && o.prec != FV_FF) || o.sigma < 0.0 || o.max_pass < 2) {
+    set_error("simple_krylov_solve_guess: bad option (prec FV_MIXED or FV_FF, max_pass >= 2)");
+    return FV_EINVAL;
+  }
+  SimpleResult r;
+  fv_status s;
+  if (o.prec == FV_FF) {
+    FV_TRY(launch_split_ff(g, U, g->Uff, g->nvel));
+    FV_TRY(launch_split_ff(g, v_in, g->xff, g->nvel));
+    FV_TRY(launch_momentum_ff(g, g->Uff, g->xff, g->vff[1], o.sigma));
+    FV_TRY(launch_div_ff(g, g->vff[1], g->r32));
+    FV_TRY(unet_guess_f32(u, g, g->r32, g->phi32));
+    s = simple_loop_ff(g, v_out, p_out, v_in, o.sigma, o.eps, o.max_pass, o.omega, &r, true, g->phi32);
+  } else {
+    FV_TRY(launch_round_f32(g, U, g->U32, g->nvel));
+    FV_TRY(launch_round_f32(g, v_in, g->x32, g->nvel));
+    FV_TRY(launch_momentum_f32(g, g->U32, g->x32, g->w32, o.sigma));
+    FV_TRY(launch_div_f32(g, g->w32, g->r32));
+    FV_TRY(unet_guess_f32(u, g, g->r32, g->phi32));
+    s = simple_loop_ff(g, v_out, p_out, v_in, o.sigma, o.eps, o.max_pass, o.omega, &r, false, g->phi32);
+  }
+  if (stats) {
+    stats->passes = r.passes;
+    stats->phi_first = r.phi_first;
+    stats->phi_last = r.phi_last;
+    stats->div_max = r.div_max;
+  }
+  if (s == FV_OK) FV_CUDA(cudaStreamSynchronize(g->stream));
+  return s;
+}
+
+fv_status ns_divergence(const fv_grid* g, const double* v, double* r) {
+  FV_TRY(check_grid(g, "ns_divergence"));
+  if (!v || !r) { set_error("ns_divergence: NULL pointer"); return FV_EINVAL; }
+  return launch_divergence(g, v, r, nullptr);
 }
 
 // ---------------------------------------------------------------- Newton --

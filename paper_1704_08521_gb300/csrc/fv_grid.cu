@@ -278,6 +278,7 @@ static fv_status build(fv_grid* g) {
   FV_TRY(upload_metrics<float>(g, &g->d_met_f, g->met_f));
   FV_TRY(upload_tpf<double>(g, &g->d_tpf_d, g->tpf_d));
   FV_TRY(upload_tpf<float>(g, &g->d_tpf_f, g->tpf_f));
+  FV_TRY(build_tc_frags(g));
   for (int i = 0; i < 3; ++i) FV_TRY(alloc(g, (void**)&g->vel_buf[i], g->nvel * sizeof(double)));
   for (int i = 0; i < 3; ++i) FV_TRY(alloc(g, (void**)&g->cell_buf[i], g->ncell * sizeof(double)));
   for (int i = 0; i < 2; ++i) FV_TRY(alloc(g, &g->tpf_buf[i], g->ncell * sizeof(double)));
@@ -449,7 +450,7 @@ void fv_grid_destroy(fv_grid* g) {
                   g->vel_buf[2], g->cell_buf[0], g->cell_buf[1], g->cell_buf[2], g->tpf_buf[0],
                   g->tpf_buf[1], g->d_scal, g->d_part, g->kry, g->kry_small, g->U32, g->x32,
                   g->w32, g->vff[0], g->vff[1], g->pff, g->r32, g->phi32, g->d_met_ff,
-                  g->d_met_fn, g->Uff, g->xff};
+                  g->d_met_fn, g->Uff, g->xff, g->d_tc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_scal) cudaFreeHost(g->h_scal);

@@ -78,6 +78,21 @@ struct TpfDev {
   const T* Einvt[3];   // the fused shared-memory transform kernels
 };
 
+// Tensor-core operands of the fused float32 pressure solve (every n <= 128):
+// the eigenbases split into TF32 hi + lo parts, stored in the lane order of
+// mma.m16n8k8 so that each lane fetches its fragment with vector loads.
+//   B layout (x axis, B[k = i][n = a] = M[a][i]): [nt][ks][lane] float4
+//     {b0 hi, b1 hi, b0 lo, b1 lo}, nt, ks < up8(n) / 8
+//   A layout (y, z axes, A[m = r][k = c] = M[r][c]): [mt][ks][lane][2] float4
+//     {a0..a3 hi}, {a0..a3 lo}, mt < up16(n) / 16, ks < up8(n) / 8
+// Index 0 holds the forward basis Einv, index 1 the inverse basis E.
+struct TcFrags {
+  bool ready = false;
+  const float4* bx[2] = {nullptr, nullptr};
+  const float4* ay[2] = {nullptr, nullptr};
+  const float4* az[2] = {nullptr, nullptr};
+};
+
 // device-side state of one SIMPLE loop (graph path)
 struct LoopState {
   float phi1, phi_prev, phi_last, div_last;
@@ -118,6 +133,8 @@ struct fv_grid {
   fv::Met<float> met_f;
   fv::TpfDev<double> tpf_d;
   fv::TpfDev<float> tpf_f;
+  void* d_tc = nullptr;      // tensor-core fragments of the fused pressure solve
+  fv::TcFrags tc;
 
   // workspace
   double* vel_buf[3] = {nullptr, nullptr, nullptr};   // n_vel each
@@ -243,6 +260,8 @@ void destroy_graph_cache(GraphCache& c);
 // tensor-product pressure solve: phi = (D G)^+ r ; phi is float or double
 fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec);
 fv_status tpf_solve_f32(const fv_grid* g, const float* r, float* phi);
+// builds g->tc when every dimension is <= 128 (fv_poisson.cu)
+fv_status build_tc_frags(fv_grid* g);
 // learned first pass of the SIMPLE loop (fv_unet.cu): phi = guess for r
 fv_status unet_guess_f32(fv_unet* u, const fv_grid* g, const float* r, float* phi);
 // max |x[0..n)| of a float32 array to the host (synchronises g's stream)

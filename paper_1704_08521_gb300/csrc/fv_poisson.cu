@@ -7,6 +7,9 @@
 // register-tiled shared-memory kernel (64 x 64 outputs per block, 4 x 4 per
 // thread); the eigenvalue scaling is fused into the epilogue of the third
 // forward transform.  float32 in the mixed mode, float64 otherwise.
+#include <cstring>
+#include <vector>
+
 #include "fv_ff.cuh"
 #include "fv_internal.cuh"
 
@@ -317,239 +320,421 @@ fv_status run_left(const fv_grid* g, int axis, const T* M, const TI* in, TO* out
 // shared load); the plane or column block is read from and written to
 // global memory exactly once per kernel.
 constexpr int kFusedMax = 128;
-constexpr int kColGroup = 64;
 
-__host__ __device__ __forceinline__ int up4(int n) { return (n + 3) & ~3; }
 __host__ __device__ __forceinline__ int up8(int n) { return (n + 7) & ~7; }
 
-// rows per thread of the fused kernels' register tiles (8 x 4 outputs:
-// three float4 shared loads per 32 FMAs)
-constexpr int RT = 8;
+// The fused kernels run the dense contractions on the tensor cores
+// (mma.sync m16n8k8, TF32 operands, float32 accumulation) with every operand
+// split into TF32 hi + lo parts and three products per tile,
+//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi   (the a_lo b_lo term is below
+// float32 round-off), which keeps the transforms at float32-level accuracy
+// (~22 significant bits) while using the tensor pipes instead of the FP32
+// lanes.  The eigenbases come pre-split in fragment order (TcFrags); field
+// values are split when staged in shared memory or when loaded into a
+// fragment.
 
-// acc[r][c] += sum_k At[k*lda + RT*tr + r] * Bt[k*ldb + 4*tc + c]
-__device__ __forceinline__ void smem_mm(const float* At, int lda, const float* Bt, int ldb, int K,
-                                        int tr, int tc, float (&acc)[RT][4]) {
-#pragma unroll 2
-  for (int k = 0; k < K; ++k) {
-    const float4 a0 = *reinterpret_cast<const float4*>(At + k * lda + RT * tr);
-    const float4 a1 = *reinterpret_cast<const float4*>(At + k * lda + RT * tr + 4);
-    const float4 b = *reinterpret_cast<const float4*>(Bt + k * ldb + 4 * tc);
-    const float av[RT] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-    for (int r = 0; r < RT; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
-  }
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
 }
 
-// out[k][:, a0:a1] = M2 (in[k] M1[a0:a1, :]^T) for the (ny x nx) plane k and
-// the column range of blockIdx.y (the plane's columns are split over
-// gridDim.y blocks so that all SMs get work); M1t = M1^T (nx x nx), M2t =
-// M2^T (ny x ny), both row-major.  Threads: (ceil(ny/4), ceil(ncol/4)).
-__global__ void k_slab_xy(const float* __restrict__ in, float* __restrict__ out,
-                          const float* __restrict__ M1t, const float* __restrict__ M2t, int nx,
-                          int ny, int ncol) {
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));   // exact difference, rounded to TF32
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t f2u(float x) { return __float_as_uint(x); }
+
+// asynchronous 4-byte global -> shared copy; zero-fills when !valid (src unread)
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+constexpr int kTcMaxNt = 8;   // n-tiles (8 columns each) per block of the slab kernel
+constexpr int kTcCols = 32;   // (x, y) columns per block of the column kernel
+
+__host__ __device__ __forceinline__ int up16(int n) { return (n + 15) & ~15; }
+
+// smallest leading dimension >= n (multiple of 8) that is 8 or 24 mod 32:
+// the B-fragment reads (rows t4, columns g) then hit 32 distinct banks
+inline int ld_b(int n) {
+  int ld = up8(n);
+  while (ld % 32 != 8 && ld % 32 != 24) ld += 8;
+  return ld;
+}
+
+// Both 1-D transforms of one (ny x nx) plane k = blockIdx.x, restricted to
+// the columns [a0, a0 + ncol) of blockIdx.y:
+//   T[j][a] = sum_i in[k][j][i] M1[a][i]     (x, tensor cores, B = bx frags)
+//   out[k][b][a] = sum_j M2[b][j] T[j][a]    (y, tensor cores, A = ay frags)
+// One warp per 16-row tile (blockDim = 32 * up16(ny) / 16).  Shared memory:
+// P [16 MT][ldP] (the plane, zero-padded), T hi / lo [16 MT][ldT].
+__global__ void __launch_bounds__(256) k_slab_xy_tc(const float* __restrict__ in,
+                                                    float* __restrict__ out,
+                                                    const float4* __restrict__ bx,
+                                                    const float4* __restrict__ ay, int nx, int ny,
+                                                    int ncol, int ldP, int ldT) {
   extern __shared__ __align__(16) float sm[];
+  const int MT = blockDim.x >> 5;
+  const int KS1 = up8(nx) >> 3, KS2 = up8(ny) >> 3;
+  float* P = sm;
+  float* Th = P + 16 * MT * ldP;
+  float* Tl = Th + 16 * MT * ldT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
   const int a0 = blockIdx.y * ncol;
-  const int na = min(ncol, nx - a0);
-  const int ncp = up4(ncol), nyp = up8(ny);
-  const int nmax = nx > ny ? nx : ny;
-  float* A1 = sm;                      // in^T  [nx][nyp]; later M2t [ny][nyp]
-  float* B1 = A1 + nmax * nyp;         // M1t[:, a0:a1]  [nx][ncp]
-  float* T = B1 + nx * ncp;            // T     [nyp][ncp] (padded rows unused)
-  const int nthr = blockDim.x;
-  const int tid = threadIdx.x;
-  const int tc = tid % (ncp / 4), tr = tid / (ncp / 4);
+  const int nt0 = a0 >> 3;
+  const int ntc = min(ncol >> 3, KS1 - nt0);
+  const int kp = up8(nx);
   const float* ink = in + (int64_t)blockIdx.x * nx * ny;
-  {
-    // (j, i) of element e = tid + s * nthr advanced without division
-    const int dj = nthr / nx, di = nthr - dj * nx;
-    int j = tid / nx, i = tid - j * nx;
-#pragma unroll 4
-    for (int e = tid; e < nx * ny; e += nthr) {
-      A1[i * nyp + j] = ink[e];
-      i += di;
-      j += dj;
-      if (i >= nx) { i -= nx; ++j; }
+  for (int j = warp; j < 16 * MT; j += MT)
+    for (int i = lane; i < kp; i += 32) {
+      const bool ok = j < ny && i < nx;
+      cp_async4(P + j * ldP + i, ok ? ink + j * nx + i : ink, ok);
     }
-  }
-  {
-    const int dr = nthr / ncol, dc = nthr - dr * ncol;
-    int r = tid / ncol, c = tid - r * ncol;
-#pragma unroll 4
-    for (int e = tid; e < nx * ncol; e += nthr) {
-      B1[r * ncp + c] = (c < na) ? M1t[r * nx + a0 + c] : 0.f;
-      c += dc;
-      r += dr;
-      if (c >= ncol) { c -= ncol; ++r; }
-    }
-  }
+  cp_async_wait_all();
   __syncthreads();
-  float acc[RT][4] = {};
-  smem_mm(A1, nyp, B1, ncp, nx, tr, tc, acc);       // T[j][a] = sum_i in[j][i] M1[a][i]
+
+  float acc[kTcMaxNt][4];
 #pragma unroll
-  for (int r = 0; r < RT; ++r)
+  for (int n = 0; n < kTcMaxNt; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  const float* Pw = P + (16 * warp + g) * ldP + t4;
+  const float4* bw = bx + (size_t)nt0 * KS1 * 32 + lane;   // [n][ks] stride KS1 * 32
+  float4 bcur[kTcMaxNt], bnxt[kTcMaxNt];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) T[(RT * tr + r) * ncp + 4 * tc + c] = acc[r][c];
-  __syncthreads();
+  for (int n = 0; n < kTcMaxNt; ++n)
+    if (n < ntc) bcur[n] = __ldg(bw + (size_t)n * KS1 * 32);
+  for (int ks = 0; ks < KS1; ++ks) {
+    if (ks + 1 < KS1) {
+#pragma unroll
+      for (int n = 0; n < kTcMaxNt; ++n)
+        if (n < ntc) bnxt[n] = __ldg(bw + (size_t)n * KS1 * 32 + (ks + 1) * 32);
+    }
+    uint32_t ah[4], al[4];
+    split_tf32(Pw[8 * ks], ah[0], al[0]);
+    split_tf32(Pw[8 * ks + 8 * ldP], ah[1], al[1]);
+    split_tf32(Pw[8 * ks + 4], ah[2], al[2]);
+    split_tf32(Pw[8 * ks + 8 * ldP + 4], ah[3], al[3]);
+    // the three products sweep the n-tiles in turn: consecutive mma on one
+    // accumulator are ntc instructions apart
+#pragma unroll
+    for (int n = 0; n < kTcMaxNt; ++n)
+      if (n < ntc) mma_tf32(acc[n], al, f2u(bcur[n].x), f2u(bcur[n].y));
+#pragma unroll
+    for (int n = 0; n < kTcMaxNt; ++n)
+      if (n < ntc) mma_tf32(acc[n], ah, f2u(bcur[n].z), f2u(bcur[n].w));
+#pragma unroll
+    for (int n = 0; n < kTcMaxNt; ++n)
+      if (n < ntc) {
+        mma_tf32(acc[n], ah, f2u(bcur[n].x), f2u(bcur[n].y));
+        bcur[n] = bnxt[n];
+      }
+  }
   {
-    const int dj = nthr / ny, db = nthr - dj * ny;
-    int j = tid / ny, b = tid - j * ny;
-#pragma unroll 4
-    for (int e = tid; e < ny * ny; e += nthr) {
-      A1[j * nyp + b] = M2t[e];
-      b += db;
-      j += dj;
-      if (b >= ny) { b -= ny; ++j; }
+    const int r0 = 16 * warp + g;
+#pragma unroll
+    for (int n = 0; n < kTcMaxNt; ++n) {
+      if (n < ntc) {
+        const int c = 8 * n + 2 * t4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int o = (r0 + 8 * (q >> 1)) * ldT + c + (q & 1);
+          uint32_t h, l;
+          split_tf32(acc[n][q], h, l);
+          Th[o] = __uint_as_float(h);
+          Tl[o] = __uint_as_float(l);
+        }
+      }
     }
   }
   __syncthreads();
-  float acc2[RT][4] = {};
-  smem_mm(A1, nyp, T, ncp, ny, tr, tc, acc2);       // out[b][a] = sum_j M2[b][j] T[j][a]
+
+#pragma unroll
+  for (int n = 0; n < kTcMaxNt; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  const float4* aw = ay + (size_t)warp * KS2 * 64 + 2 * lane;
+  float4 h4n = __ldg(aw), l4n = __ldg(aw + 1);
+  for (int ks = 0; ks < KS2; ++ks) {
+    const float4 h4 = h4n, l4 = l4n;
+    if (ks + 1 < KS2) {
+      h4n = __ldg(aw + (ks + 1) * 64);
+      l4n = __ldg(aw + (ks + 1) * 64 + 1);
+    }
+    const uint32_t ah[4] = {f2u(h4.x), f2u(h4.y), f2u(h4.z), f2u(h4.w)};
+    const uint32_t al[4] = {f2u(l4.x), f2u(l4.y), f2u(l4.z), f2u(l4.w)};
+    const int o = (8 * ks + t4) * ldT + g;
+    uint32_t bh[kTcMaxNt][2], bl[kTcMaxNt][2];
+#pragma unroll
+    for (int n = 0; n < kTcMaxNt; ++n)
+      if (n < ntc) {
+        const int on = o + 8 * n;
+        bh[n][0] = f2u(Th[on]);
+        bh[n][1] = f2u(Th[on + 4 * ldT]);
+        bl[n][0] = f2u(Tl[on]);
+        bl[n][1] = f2u(Tl[on + 4 * ldT]);
+      }
+#pragma unroll
+    for (int n = 0; n < kTcMaxNt; ++n)
+      if (n < ntc) mma_tf32(acc[n], al, bh[n][0], bh[n][1]);
+#pragma unroll
+    for (int n = 0; n < kTcMaxNt; ++n)
+      if (n < ntc) mma_tf32(acc[n], ah, bl[n][0], bl[n][1]);
+#pragma unroll
+    for (int n = 0; n < kTcMaxNt; ++n)
+      if (n < ntc) mma_tf32(acc[n], ah, bh[n][0], bh[n][1]);
+  }
   float* outk = out + (int64_t)blockIdx.x * nx * ny;
+  const int b0 = 16 * warp + g;
 #pragma unroll
-  for (int r = 0; r < RT; ++r) {
-    const int b = RT * tr + r;
-    if (b >= ny) continue;
+  for (int n = 0; n < kTcMaxNt; ++n) {
+    if (n < ntc) {
+      const int a = a0 + 8 * n + 2 * t4;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int a = 4 * tc + c;
-      if (a < na) outk[b * nx + a0 + a] = acc2[r][c];
+      for (int q = 0; q < 4; ++q) {
+        const int b = b0 + 8 * (q >> 1), aa = a + (q & 1);
+        if (b < ny && aa < nx) outk[b * nx + aa] = acc[n][q];
+      }
     }
   }
 }
 
-// z-direction forward transform, eigenvalue scaling and inverse transform for
-// 64 (x,y) columns.  Threads: (ceil(nz/4), 16).
-__global__ void k_col_z(const float* __restrict__ in, float* __restrict__ out, TpfDev<float> tp) {
+// z-direction forward transform, eigenvalue scaling and inverse transform of
+// kTcCols (x, y) columns q0 + [0, kTcCols), q = j nx + i:
+//   t[c][q] = sum_k Ez^-1[c][k] in[k][q] / (lam_z[c] + lam_y[j] + lam_x[i])   (null mode -> 0)
+//   out[m][q] = sum_c Ez[m][c] t[c][q]
+// One warp per 16-row tile (blockDim = 32 * up16(nz) / 16).  Shared memory:
+// X hi / lo [16 MT][ldX] (input, then t), lam_x + lam_y and the null flag per column.
+__global__ void __launch_bounds__(256) k_col_z_tc(const float* __restrict__ in,
+                                                  float* __restrict__ out, TpfDev<float> tp,
+                                                  const float4* __restrict__ azi,
+                                                  const float4* __restrict__ aze, int ldX) {
   extern __shared__ __align__(16) float sm[];
   const int nx = tp.n[0], ny = tp.n[1], nz = tp.n[2];
-  const int nzp = up8(nz);
+  const int MT = blockDim.x >> 5, KS = up8(nz) >> 3;
   const int64_t Q = (int64_t)nx * ny;
-  const int64_t q0 = (int64_t)blockIdx.x * kColGroup;
-  float* X = sm;                        // in tile   [nz][64]
-  float* Mz = X + nz * kColGroup;       // Ez^-T / Ez^T [nz][nzp]
-  float* Tt = Mz + nz * nzp;            // scaled     [nzp][64]
-  const int nthr = blockDim.x, tid = threadIdx.x;
-  const int tc = tid & 15, tr = tid >> 4;
-#pragma unroll 8
-  for (int e = tid; e < nz * kColGroup; e += nthr) {
-    const int k = e >> 6, qq = e & 63;   // power-of-two split: shifts only
-    const int64_t q = q0 + qq;
-    X[e] = (q < Q) ? in[(int64_t)k * Q + q] : 0.f;
-  }
-  const float* Zi = tp.Einvt[2];
-  {
-    const int dk = nthr / nz, dc = nthr - dk * nz;
-    int k = tid / nz, c = tid - k * nz;
-#pragma unroll 4
-    for (int e = tid; e < nz * nz; e += nthr) {
-      Mz[k * nzp + c] = Zi[e];
-      c += dc;
-      k += dk;
-      if (c >= nz) { c -= nz; ++k; }
+  const int64_t q0 = (int64_t)blockIdx.x * kTcCols;
+  float* Xh = sm;
+  float* Xl = Xh + 16 * MT * ldX;
+  float* lamq = Xl + 16 * MT * ldX;
+  int* nullq = reinterpret_cast<int*>(lamq + kTcCols);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+  for (int k = warp; k < 16 * MT; k += MT)
+    for (int q = lane; q < kTcCols; q += 32) {
+      const bool ok = k < nz && q0 + q < Q;
+      cp_async4(Xh + k * ldX + q, ok ? in + k * Q + q0 + q : in, ok);
     }
+  for (int q = tid; q < kTcCols; q += blockDim.x) {
+    const int64_t qq = q0 + q;
+    float lq = 1.f;
+    int nl = 0;
+    if (qq < Q) {
+      const int ia = (int)(qq % nx), jb = (int)(qq / nx);
+      lq = tp.lam[0][ia] + tp.lam[1][jb];
+      nl = (ia == tp.null_index[0] && jb == tp.null_index[1]);
+    }
+    lamq[q] = lq;
+    nullq[q] = nl;
   }
+  cp_async_wait_all();
+  // each thread splits the elements it copied (same indices as the copy loop)
+  for (int k = warp; k < 16 * MT; k += MT)
+    for (int q = lane; q < kTcCols; q += 32) {
+      uint32_t h, l;
+      split_tf32(Xh[k * ldX + q], h, l);
+      Xh[k * ldX + q] = __uint_as_float(h);
+      Xl[k * ldX + q] = __uint_as_float(l);
+    }
   __syncthreads();
-  float acc[RT][4] = {};
-  smem_mm(Mz, nzp, X, kColGroup, nz, tr, tc, acc);   // t[c][q] = sum_k Ez^-1[c][k] in[k][q]
+
+  constexpr int NT = kTcCols / 8;
+  float acc[NT][4];
 #pragma unroll
-  for (int r = 0; r < RT; ++r) {
-    const int c = RT * tr + r;
+  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  const float4* aw = azi + (size_t)warp * KS * 64 + 2 * lane;
+  float4 h4n = __ldg(aw), l4n = __ldg(aw + 1);
+  for (int ks = 0; ks < KS; ++ks) {
+    const float4 h4 = h4n, l4 = l4n;
+    if (ks + 1 < KS) {
+      h4n = __ldg(aw + (ks + 1) * 64);
+      l4n = __ldg(aw + (ks + 1) * 64 + 1);
+    }
+    const uint32_t ah[4] = {f2u(h4.x), f2u(h4.y), f2u(h4.z), f2u(h4.w)};
+    const uint32_t al[4] = {f2u(l4.x), f2u(l4.y), f2u(l4.z), f2u(l4.w)};
+    const int o = (8 * ks + t4) * ldX + g;
+    uint32_t bh[NT][2], bl[NT][2];
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const int64_t q = q0 + 4 * tc + cc;
-      float v = 0.f;
-      if (c < nz && q < Q) {
-        const int ia = (int)(q % nx), jb = (int)(q / nx);
-        if (!(c == tp.null_index[2] && jb == tp.null_index[1] && ia == tp.null_index[0]))
-          v = acc[r][cc] / (tp.lam[2][c] + tp.lam[1][jb] + tp.lam[0][ia]);
+    for (int n = 0; n < NT; ++n) {
+      const int on = o + 8 * n;
+      bh[n][0] = f2u(Xh[on]);
+      bh[n][1] = f2u(Xh[on + 4 * ldX]);
+      bl[n][0] = f2u(Xl[on]);
+      bl[n][1] = f2u(Xl[on + 4 * ldX]);
+    }
+#pragma unroll
+    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], al, bh[n][0], bh[n][1]);
+#pragma unroll
+    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], ah, bl[n][0], bl[n][1]);
+#pragma unroll
+    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], ah, bh[n][0], bh[n][1]);
+  }
+  __syncthreads();   // every warp is done reading X: t overwrites it
+  {
+    const int c0 = 16 * warp + g;
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + 8 * (q >> 1), col = 8 * n + 2 * t4 + (q & 1);
+        float v = 0.f;
+        if (c < nz && q0 + col < Q && !(c == tp.null_index[2] && nullq[col]))
+          v = acc[n][q] / (tp.lam[2][c] + lamq[col]);
+        uint32_t h, l;
+        split_tf32(v, h, l);
+        Xh[c * ldX + col] = __uint_as_float(h);
+        Xl[c * ldX + col] = __uint_as_float(l);
       }
-      Tt[c * kColGroup + 4 * tc + cc] = v;
     }
   }
   __syncthreads();
-  const float* Ze = tp.Et[2];
-  {
-    const int dc = nthr / nz, dm = nthr - dc * nz;
-    int c = tid / nz, m = tid - c * nz;
-#pragma unroll 4
-    for (int e = tid; e < nz * nz; e += nthr) {
-      Mz[c * nzp + m] = Ze[e];
-      m += dm;
-      c += dc;
-      if (m >= nz) { m -= nz; ++c; }
+
+#pragma unroll
+  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  aw = aze + (size_t)warp * KS * 64 + 2 * lane;
+  h4n = __ldg(aw);
+  l4n = __ldg(aw + 1);
+  for (int ks = 0; ks < KS; ++ks) {
+    const float4 h4 = h4n, l4 = l4n;
+    if (ks + 1 < KS) {
+      h4n = __ldg(aw + (ks + 1) * 64);
+      l4n = __ldg(aw + (ks + 1) * 64 + 1);
+    }
+    const uint32_t ah[4] = {f2u(h4.x), f2u(h4.y), f2u(h4.z), f2u(h4.w)};
+    const uint32_t al[4] = {f2u(l4.x), f2u(l4.y), f2u(l4.z), f2u(l4.w)};
+    const int o = (8 * ks + t4) * ldX + g;
+    uint32_t bh[NT][2], bl[NT][2];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+      const int on = o + 8 * n;
+      bh[n][0] = f2u(Xh[on]);
+      bh[n][1] = f2u(Xh[on + 4 * ldX]);
+      bl[n][0] = f2u(Xl[on]);
+      bl[n][1] = f2u(Xl[on + 4 * ldX]);
+    }
+#pragma unroll
+    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], al, bh[n][0], bh[n][1]);
+#pragma unroll
+    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], ah, bl[n][0], bl[n][1]);
+#pragma unroll
+    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], ah, bh[n][0], bh[n][1]);
+  }
+  const int m0 = 16 * warp + g;
+#pragma unroll
+  for (int n = 0; n < NT; ++n) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = m0 + 8 * (q >> 1);
+      const int64_t col = q0 + 8 * n + 2 * t4 + (q & 1);
+      if (m < nz && col < Q) out[m * Q + col] = acc[n][q];
     }
   }
-  __syncthreads();
-  float acc2[RT][4] = {};
-  smem_mm(Mz, nzp, Tt, kColGroup, nz, tr, tc, acc2);  // out[m][q] = sum_c Ez[m][c] t[c][q]
-#pragma unroll
-  for (int r = 0; r < RT; ++r) {
-    const int m = RT * tr + r;
-    if (m >= nz) continue;
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const int64_t q = q0 + 4 * tc + cc;
-      if (q < Q) out[(int64_t)m * Q + q] = acc2[r][cc];
-    }
+}
+
+// launch shapes of the fused kernels
+struct SlabShape {
+  int nsplit, ncol, ldP, ldT, threads;
+  size_t smem;
+};
+
+inline SlabShape slab_shape(int nx, int ny, int nz) {
+  SlabShape s;
+  const int kp = up8(nx);
+  // column split: at least enough for 8 n-tiles per block; among up to 4,
+  // the one whose nz * nsplit blocks fill whole waves of 2 blocks per SM best
+  const int nmin = (kp + 8 * kTcMaxNt - 1) / (8 * kTcMaxNt);
+  s.nsplit = nmin;
+  double best = -1.0;
+  for (int ns = nmin; ns <= 4 && 8 * ns <= kp; ++ns) {
+    const int64_t blocks = (int64_t)nz * ns, slots = 2 * 152;
+    const double eff = (double)blocks / (double)(((blocks + slots - 1) / slots) * slots);
+    if (eff > best + 1e-9) { best = eff; s.nsplit = ns; }
   }
+  s.ncol = up8((kp + s.nsplit - 1) / s.nsplit);
+  s.ldP = kp + 4;                 // ldP / 4 odd: the A-fragment reads hit 32 banks
+  s.ldT = ld_b(s.ncol);
+  s.threads = 32 * (up16(ny) / 16);
+  s.smem = sizeof(float) * (size_t)up16(ny) * (s.ldP + 2 * s.ldT);
+  return s;
 }
 
-// the columns of a plane are split over kSlabSplit blocks
-constexpr int kSlabSplit = 1;
-inline int slab_cols(int nx) { return (nx + kSlabSplit - 1) / kSlabSplit; }
+struct ColShape {
+  int ldX, threads;
+  unsigned blocks;
+  size_t smem;
+};
 
-inline size_t slab_smem(int nx, int ny) {
-  const int nmax = nx > ny ? nx : ny;
-  const int ncp = up4(slab_cols(nx));
-  return sizeof(float) * ((size_t)nmax * up8(ny) + (size_t)nx * ncp + (size_t)up8(ny) * ncp);
+inline ColShape col_shape(int nx, int ny, int nz) {
+  ColShape c;
+  c.ldX = ld_b(kTcCols);
+  c.threads = 32 * (up16(nz) / 16);
+  c.blocks = (unsigned)(((int64_t)nx * ny + kTcCols - 1) / kTcCols);
+  c.smem = sizeof(float) * ((size_t)2 * up16(nz) * c.ldX + 2 * kTcCols);
+  return c;
 }
 
-inline size_t col_smem(int nz) {
-  return sizeof(float) * ((size_t)nz * kColGroup + (size_t)nz * up8(nz) + (size_t)up8(nz) * kColGroup);
+fv_status set_tc_attributes() {
+  static bool done = false;   // the attribute is per function, not per grid
+  if (!done) {
+    FV_CUDA(cudaFuncSetAttribute(k_slab_xy_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    FV_CUDA(cudaFuncSetAttribute(k_col_z_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    done = true;
+  }
+  return FV_OK;
 }
 
-fv_status tpf_fused_f32(const fv_grid* g, const float* r, float* phi) {
+// dir 0: forward (Einv) transforms, 1: inverse (E)
+fv_status launch_slab(const fv_grid* g, const float* in, float* out, int dir) {
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-  const TpfDev<float>& tp = g->tpf_f;
-  float* a = (float*)g->tpf_buf[0];
-  float* b = (float*)g->tpf_buf[1];
-  const size_t ss = slab_smem(nx, ny), cs = col_smem(nz);
-  static bool attr_set = false;   // the attribute is per function, not per grid
-  if (!attr_set) {
-    FV_CUDA(cudaFuncSetAttribute(k_slab_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    FV_CUDA(cudaFuncSetAttribute(k_col_z, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
-  const int slab_threads = (up8(ny) / RT) * (up4(slab_cols(nx)) / 4);
-  const dim3 slab_grid(nz, kSlabSplit);
-  const int col_threads = (up8(nz) / RT) * 16;
-  const unsigned ncol = (unsigned)(((int64_t)nx * ny + kColGroup - 1) / kColGroup);
-  {
-    LaunchScope ls_(g, FV_K_TPF_X);
-    k_slab_xy<<<slab_grid, slab_threads, ss, g->stream>>>(r, a, tp.Einvt[0], tp.Einvt[1], nx, ny,
-                                                          slab_cols(nx));
-  }
-  FV_CHECK_LAUNCH();
-  {
-    LaunchScope ls_(g, FV_K_TPF_YZ);
-    k_col_z<<<ncol, col_threads, cs, g->stream>>>(a, b, tp);
-  }
-  FV_CHECK_LAUNCH();
-  {
-    LaunchScope ls_(g, FV_K_TPF_X);
-    k_slab_xy<<<slab_grid, slab_threads, ss, g->stream>>>(b, phi, tp.Et[0], tp.Et[1], nx, ny,
-                                                          slab_cols(nx));
-  }
+  const SlabShape s = slab_shape(nx, ny, nz);
+  LaunchScope ls_(g, FV_K_TPF_X);
+  k_slab_xy_tc<<<dim3(nz, s.nsplit), s.threads, s.smem, g->stream>>>(
+      in, out, g->tc.bx[dir], g->tc.ay[dir], nx, ny, s.ncol, s.ldP, s.ldT);
   FV_CHECK_LAUNCH();
   return FV_OK;
 }
 
+fv_status launch_col(const fv_grid* g, const float* in, float* out) {
+  const ColShape c = col_shape(g->n[0], g->n[1], g->n[2]);
+  LaunchScope ls_(g, FV_K_TPF_YZ);
+  k_col_z_tc<<<c.blocks, c.threads, c.smem, g->stream>>>(in, out, g->tpf_f, g->tc.az[0], g->tc.az[1],
+                                                         c.ldX);
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status tpf_fused_f32(const fv_grid* g, const float* r, float* phi) {
+  FV_TRY(set_tc_attributes());
+  float* a = (float*)g->tpf_buf[0];
+  float* b = (float*)g->tpf_buf[1];
+  FV_TRY(launch_slab(g, r, a, 0));
+  FV_TRY(launch_col(g, a, b));
+  FV_TRY(launch_slab(g, b, phi, 1));
+  return FV_OK;
+}
+
 inline bool fused_ok(const fv_grid* g) {
-  return g->n[0] <= kFusedMax && g->n[1] <= kFusedMax && g->n[2] <= kFusedMax &&
-         slab_smem(g->n[0], g->n[1]) <= 200 * 1024 && col_smem(g->n[2]) <= 200 * 1024;
+  return g->tc.ready && g->n[0] <= kFusedMax && g->n[1] <= kFusedMax && g->n[2] <= kFusedMax;
 }
 
 template <typename T, typename TI, typename TO>
@@ -567,6 +752,95 @@ fv_status tpf_run(const fv_grid* g, const TpfDev<T>& tp, const TI* r, TO* phi) {
 
 }  // namespace
 
+// TF32 value of x, rounded to nearest with ties away from zero (cvt.rna)
+static float tf32_host(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+static void split_host(double x, float& hi, float& lo) {
+  hi = tf32_host((float)x);
+  lo = tf32_host((float)(x - (double)hi));
+}
+
+// B fragments of M (n x n, row-major): B[k = i][col = a] = M[a][i]
+static void frag_b(const std::vector<double>& M, int n, float4* out) {
+  const int KS = up8(n) / 8;
+  for (int nt = 0; nt < KS; ++nt)
+    for (int ks = 0; ks < KS; ++ks)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, t4 = lane & 3;
+        const int a = 8 * nt + g, i0 = 8 * ks + t4, i1 = i0 + 4;
+        const double v0 = (a < n && i0 < n) ? M[(size_t)a * n + i0] : 0.0;
+        const double v1 = (a < n && i1 < n) ? M[(size_t)a * n + i1] : 0.0;
+        float h0, l0, h1, l1;
+        split_host(v0, h0, l0);
+        split_host(v1, h1, l1);
+        out[((size_t)nt * KS + ks) * 32 + lane] = make_float4(h0, h1, l0, l1);
+      }
+}
+
+// A fragments of M (n x n, row-major): A[row = r][k = c] = M[r][c]
+static void frag_a(const std::vector<double>& M, int n, float4* out) {
+  const int KS = up8(n) / 8, MT = up16(n) / 16;
+  for (int mt = 0; mt < MT; ++mt)
+    for (int ks = 0; ks < KS; ++ks)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, t4 = lane & 3;
+        const int r[4] = {16 * mt + g, 16 * mt + g + 8, 16 * mt + g, 16 * mt + g + 8};
+        const int c[4] = {8 * ks + t4, 8 * ks + t4, 8 * ks + t4 + 4, 8 * ks + t4 + 4};
+        float h[4], l[4];
+        for (int q = 0; q < 4; ++q)
+          split_host((r[q] < n && c[q] < n) ? M[(size_t)r[q] * n + c[q]] : 0.0, h[q], l[q]);
+        float4* o = out + (((size_t)mt * KS + ks) * 32 + lane) * 2;
+        o[0] = make_float4(h[0], h[1], h[2], h[3]);
+        o[1] = make_float4(l[0], l[1], l[2], l[3]);
+      }
+}
+
+fv_status build_tc_frags(fv_grid* g) {
+  g->tc = TcFrags();
+  for (int d = 0; d < 3; ++d)
+    if (g->n[d] > kFusedMax) return FV_OK;   // the fused kernels serve n <= 128 only
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  const size_t szb = (size_t)(up8(nx) / 8) * (up8(nx) / 8) * 32;
+  const size_t sza_y = (size_t)(up16(ny) / 16) * (up8(ny) / 8) * 64;
+  const size_t sza_z = (size_t)(up16(nz) / 16) * (up8(nz) / 8) * 64;
+  const size_t total = 2 * (szb + sza_y + sza_z);
+  std::vector<float4> h(total);
+  float4* p = h.data();
+  float4* bx[2] = {p, p + szb};
+  float4* ay[2] = {p + 2 * szb, p + 2 * szb + sza_y};
+  float4* az[2] = {p + 2 * szb + 2 * sza_y, p + 2 * szb + 2 * sza_y + sza_z};
+  frag_b(g->basis[0].Einv, nx, bx[0]);
+  frag_b(g->basis[0].E, nx, bx[1]);
+  frag_a(g->basis[1].Einv, ny, ay[0]);
+  frag_a(g->basis[1].E, ny, ay[1]);
+  frag_a(g->basis[2].Einv, nz, az[0]);
+  frag_a(g->basis[2].E, nz, az[1]);
+  cudaError_t e = cudaMalloc(&g->d_tc, total * sizeof(float4));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    g->d_tc = nullptr;
+    set_error("cudaMalloc of the tensor-core fragments failed");
+    return FV_ENOMEM;
+  }
+  g->ws_bytes += (int64_t)(total * sizeof(float4));
+  FV_CUDA(cudaMemcpy(g->d_tc, h.data(), total * sizeof(float4), cudaMemcpyHostToDevice));
+  const float4* base = (const float4*)g->d_tc;
+  for (int q = 0; q < 2; ++q) {
+    g->tc.bx[q] = base + (bx[q] - p);
+    g->tc.ay[q] = base + (ay[q] - p);
+    g->tc.az[q] = base + (az[q] - p);
+  }
+  g->tc.ready = true;
+  return FV_OK;
+}
+
 fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec) {
   if (prec == FV_MIXED) return tpf_run<float, double, float>(g, g->tpf_f, r, (float*)phi);
   return tpf_run<double, double, double>(g, g->tpf_d, r, (double*)phi);
@@ -583,19 +857,8 @@ fv_status tpf_one_transform_f32(const fv_grid* g, int axis) {
   float* a = (float*)g->tpf_buf[0];
   float* b = (float*)g->tpf_buf[1];
   if (fused_ok(g)) {          // fused kernels: axis 0 = one slab kernel, else one column kernel
-    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-    if (axis == 0) {
-      LaunchScope ls_(g, FV_K_TPF_X);
-      k_slab_xy<<<dim3(nz, kSlabSplit), (up8(ny) / RT) * (up4(slab_cols(nx)) / 4),
-                  slab_smem(nx, ny), g->stream>>>(a, b, g->tpf_f.Einvt[0], g->tpf_f.Einvt[1], nx,
-                                                  ny, slab_cols(nx));
-    } else {
-      LaunchScope ls_(g, FV_K_TPF_YZ);
-      k_col_z<<<(unsigned)(((int64_t)nx * ny + kColGroup - 1) / kColGroup), (up8(nz) / RT) * 16,
-                col_smem(nz), g->stream>>>(a, b, g->tpf_f);
-    }
-    FV_CHECK_LAUNCH();
-    return FV_OK;
+    FV_TRY(set_tc_attributes());
+    return axis == 0 ? launch_slab(g, a, b, 0) : launch_col(g, a, b);
   }
   if (axis == 0) return run_right<float, float, float>(g, g->tpf_f.Einv[0], a, b);
   return run_left<float, float, float, false>(g, axis, g->tpf_f.Einv[axis], a, b, g->tpf_f);

@@ -278,7 +278,7 @@ static fv_status build(fv_grid* g) {
   FV_TRY(upload_metrics<float>(g, &g->d_met_f, g->met_f));
   FV_TRY(upload_tpf<double>(g, &g->d_tpf_d, g->tpf_d));
   FV_TRY(upload_tpf<float>(g, &g->d_tpf_f, g->tpf_f));
-  FV_TRY(build_tc_frags(g));
+  FV_TRY(build_tc_mats(g));
   for (int i = 0; i < 3; ++i) FV_TRY(alloc(g, (void**)&g->vel_buf[i], g->nvel * sizeof(double)));
   for (int i = 0; i < 3; ++i) FV_TRY(alloc(g, (void**)&g->cell_buf[i], g->ncell * sizeof(double)));
   for (int i = 0; i < 2; ++i) FV_TRY(alloc(g, &g->tpf_buf[i], g->ncell * sizeof(double)));

@@ -79,18 +79,20 @@ struct TpfDev {
 };
 
 // Tensor-core operands of the fused float32 pressure solve (every n <= 128):
-// the eigenbases split into TF32 hi + lo parts, stored in the lane order of
-// mma.m16n8k8 so that each lane fetches its fragment with vector loads.
-//   B layout (x axis, B[k = i][n = a] = M[a][i]): [nt][ks][lane] float4
-//     {b0 hi, b1 hi, b0 lo, b1 lo}, nt, ks < up8(n) / 8
-//   A layout (y, z axes, A[m = r][k = c] = M[r][c]): [mt][ks][lane][2] float4
-//     {a0..a3 hi}, {a0..a3 lo}, mt < up16(n) / 16, ks < up8(n) / 8
-// Index 0 holds the forward basis Einv, index 1 the inverse basis E.
-struct TcFrags {
+// the eigenbases split into TF32 hi + lo parts and stored in the canonical
+// K-major layout of fv_tc5.cuh, ready for 16-byte copies into shared memory.
+//   bx[dir]: slab_nsplit column chunks, each [hi | lo] of 128 x up8(nx),
+//            element (a, i) = M[a0 + a][i] for a < slab_n (M = Einv_x for dir 0,
+//            E_x for 1), zero rows beyond
+//   ay[dir]: [hi | lo] of 128 x up8(ny), element (b, j) = M[b][j] (Einv_y / E_y)
+//   az[0], az[1]: [hi | lo] of 128 x up8(nz) of Einv_z and E_z
+struct TcMats {
   bool ready = false;
-  const float4* bx[2] = {nullptr, nullptr};
-  const float4* ay[2] = {nullptr, nullptr};
-  const float4* az[2] = {nullptr, nullptr};
+  int slab_nsplit = 1, slab_n = 0;   // column chunks of the slab kernel, chunk width
+  int col_n = 0;                     // (x, y) columns per block of the column kernel
+  const float* bx[2] = {nullptr, nullptr};
+  const float* ay[2] = {nullptr, nullptr};
+  const float* az[2] = {nullptr, nullptr};
 };
 
 // device-side state of one SIMPLE loop (graph path)
@@ -133,8 +135,8 @@ struct fv_grid {
   fv::Met<float> met_f;
   fv::TpfDev<double> tpf_d;
   fv::TpfDev<float> tpf_f;
-  void* d_tc = nullptr;      // tensor-core fragments of the fused pressure solve
-  fv::TcFrags tc;
+  void* d_tc = nullptr;      // tensor-core operands of the fused pressure solve
+  fv::TcMats tc;
 
   // workspace
   double* vel_buf[3] = {nullptr, nullptr, nullptr};   // n_vel each
@@ -261,7 +263,7 @@ void destroy_graph_cache(GraphCache& c);
 fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec);
 fv_status tpf_solve_f32(const fv_grid* g, const float* r, float* phi);
 // builds g->tc when every dimension is <= 128 (fv_poisson.cu)
-fv_status build_tc_frags(fv_grid* g);
+fv_status build_tc_mats(fv_grid* g);
 // learned first pass of the SIMPLE loop (fv_unet.cu): phi = guess for r
 fv_status unet_guess_f32(fv_unet* u, const fv_grid* g, const float* r, float* phi);
 // max |x[0..n)| of a float32 array to the host (synchronises g's stream)

@@ -12,6 +12,7 @@
 
 #include "fv_ff.cuh"
 #include "fv_internal.cuh"
+#include "fv_tc5.cuh"
 
 namespace fv {
 
@@ -323,15 +324,17 @@ constexpr int kFusedMax = 128;
 
 __host__ __device__ __forceinline__ int up8(int n) { return (n + 7) & ~7; }
 
-// The fused kernels run the dense contractions on the tensor cores
-// (mma.sync m16n8k8, TF32 operands, float32 accumulation) with every operand
-// split into TF32 hi + lo parts and three products per tile,
-//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi   (the a_lo b_lo term is below
-// float32 round-off), which keeps the transforms at float32-level accuracy
-// (~22 significant bits) while using the tensor pipes instead of the FP32
-// lanes.  The eigenbases come pre-split in fragment order (TcFrags); field
-// values are split when staged in shared memory or when loaded into a
-// fragment.
+// The fused kernels run the dense contractions on the 5th-generation tensor
+// cores (tcgen05.mma kind::tf32, accumulators in tensor memory) with every
+// operand split into TF32 hi + lo parts and three products per product,
+//   a b ~ a_lo b_hi + a_hi b_lo + a_hi b_hi   (a_lo b_lo is below float32
+// round-off), which keeps the transforms at float32-level accuracy (~22
+// significant bits).  One block owns a 128-row accumulator (rows padded to
+// 128); one thread issues the MMAs and commits them to an mbarrier that the
+// block waits on (with an iteration limit: on timeout the outputs become NaN,
+// which the SIMPLE loop reports).  The eigenbases come pre-split and
+// pre-laid-out (TcMats) and are copied to shared memory with 16-byte
+// cp.async; field values are split by the threads that store them.
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
   uint32_t r;
@@ -339,203 +342,235 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(x - __uint_as_float(hi));   // exact difference, rounded to TF32
+__device__ __forceinline__ void split_store(float x, float* hi, float* lo) {
+  const uint32_t h = tf32_rna(x);
+  *hi = __uint_as_float(h);
+  *lo = __uint_as_float(tf32_rna(x - __uint_as_float(h)));   // exact difference, rounded to TF32
 }
 
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ uint32_t f2u(float x) { return __float_as_uint(x); }
-
-// asynchronous 4-byte global -> shared copy; zero-fills when !valid (src unread)
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
-               : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-constexpr int kTcMaxNt = 8;   // n-tiles (8 columns each) per block of the slab kernel
-constexpr int kTcCols = 32;   // (x, y) columns per block of the column kernel
+constexpr int kMbarLimit = 1 << 22;   // polls of an mbarrier before the block gives up
 
 __host__ __device__ __forceinline__ int up16(int n) { return (n + 15) & ~15; }
 
-// smallest leading dimension >= n (multiple of 8) that is 8 or 24 mod 32:
-// the B-fragment reads (rows t4, columns g) then hit 32 distinct banks
-inline int ld_b(int n) {
-  int ld = up8(n);
-  while (ld % 32 != 8 && ld % 32 != 24) ld += 8;
-  return ld;
+inline uint32_t tmem_cols(int n) {
+  uint32_t c = 32;
+  while ((int)c < n) c <<= 1;
+  return c;
 }
 
-// Both 1-D transforms of one (ny x nx) plane k = blockIdx.x, restricted to
-// the columns [a0, a0 + ncol) of blockIdx.y:
-//   T[j][a] = sum_i in[k][j][i] M1[a][i]     (x, tensor cores, B = bx frags)
-//   out[k][b][a] = sum_j M2[b][j] T[j][a]    (y, tensor cores, A = ay frags)
-// One warp per 16-row tile (blockDim = 32 * up16(ny) / 16).  Shared memory:
-// P [16 MT][ldP] (the plane, zero-padded), T hi / lo [16 MT][ldT].
-__global__ void __launch_bounds__(256) k_slab_xy_tc(const float* __restrict__ in,
-                                                    float* __restrict__ out,
-                                                    const float4* __restrict__ bx,
-                                                    const float4* __restrict__ ay, int nx, int ny,
-                                                    int ncol, int ldP, int ldT) {
-  extern __shared__ __align__(16) float sm[];
-  const int MT = blockDim.x >> 5;
-  const int KS1 = up8(nx) >> 3, KS2 = up8(ny) >> 3;
-  float* P = sm;
-  float* Th = P + 16 * MT * ldP;
-  float* Tl = Th + 16 * MT * ldT;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
-  const int a0 = blockIdx.y * ncol;
-  const int nt0 = a0 >> 3;
-  const int ntc = min(ncol >> 3, KS1 - nt0);
-  const int kp = up8(nx);
-  const float* ink = in + (int64_t)blockIdx.x * nx * ny;
-  for (int j = warp; j < 16 * MT; j += MT)
-    for (int i = lane; i < kp; i += 32) {
-      const bool ok = j < ny && i < nx;
-      cp_async4(P + j * ldP + i, ok ? ink + j * nx + i : ink, ok);
-    }
-  cp_async_wait_all();
-  __syncthreads();
+// copy [hi | lo] (2 * count floats, contiguous) into two shared arrays
+__device__ __forceinline__ void stage_pair(const float* __restrict__ src, float* hi, float* lo, int count,
+                                           int tid, int nthr) {
+  const int half = count >> 2;   // float4 per half
+  for (int e = tid; e < 2 * half; e += nthr)
+    tc5::cp_async16(e < half ? hi + 4 * e : lo + 4 * (e - half), src + 4 * e);
+}
 
-  float acc[kTcMaxNt][4];
-#pragma unroll
-  for (int n = 0; n < kTcMaxNt; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  const float* Pw = P + (16 * warp + g) * ldP + t4;
-  const float4* bw = bx + (size_t)nt0 * KS1 * 32 + lane;   // [n][ks] stride KS1 * 32
-  float4 bcur[kTcMaxNt], bnxt[kTcMaxNt];
-#pragma unroll
-  for (int n = 0; n < kTcMaxNt; ++n)
-    if (n < ntc) bcur[n] = __ldg(bw + (size_t)n * KS1 * 32);
-  for (int ks = 0; ks < KS1; ++ks) {
-    if (ks + 1 < KS1) {
-#pragma unroll
-      for (int n = 0; n < kTcMaxNt; ++n)
-        if (n < ntc) bnxt[n] = __ldg(bw + (size_t)n * KS1 * 32 + (ks + 1) * 32);
-    }
-    uint32_t ah[4], al[4];
-    split_tf32(Pw[8 * ks], ah[0], al[0]);
-    split_tf32(Pw[8 * ks + 8 * ldP], ah[1], al[1]);
-    split_tf32(Pw[8 * ks + 4], ah[2], al[2]);
-    split_tf32(Pw[8 * ks + 8 * ldP + 4], ah[3], al[3]);
-    // the three products sweep the n-tiles in turn: consecutive mma on one
-    // accumulator are ntc instructions apart
-#pragma unroll
-    for (int n = 0; n < kTcMaxNt; ++n)
-      if (n < ntc) mma_tf32(acc[n], al, f2u(bcur[n].x), f2u(bcur[n].y));
-#pragma unroll
-    for (int n = 0; n < kTcMaxNt; ++n)
-      if (n < ntc) mma_tf32(acc[n], ah, f2u(bcur[n].z), f2u(bcur[n].w));
-#pragma unroll
-    for (int n = 0; n < kTcMaxNt; ++n)
-      if (n < ntc) {
-        mma_tf32(acc[n], ah, f2u(bcur[n].x), f2u(bcur[n].y));
-        bcur[n] = bnxt[n];
-      }
+// issue D (+)= A B^T over K (multiple of 8) as three split products per step
+__device__ __forceinline__ void issue_split_gemm(uint32_t tmem, const float* Ah, const float* Al,
+                                                 const float* Bh, const float* Bl, int K, int N) {
+  const uint32_t idesc = tc5::idesc_tf32(128, N);
+  const uint32_t sbo = (uint32_t)(K / 4) * 128;
+  const uint32_t ah = tc5::smem_u32(Ah), al = tc5::smem_u32(Al), bh = tc5::smem_u32(Bh),
+                 bl = tc5::smem_u32(Bl);
+  for (int ks = 0; ks < K / 8; ++ks) {
+    const uint32_t off = (uint32_t)ks * 256;   // 8 elements of K: two 16-byte core-matrix columns
+    tc5::mma_tf32(tmem, tc5::sdesc(al + off, 128, sbo), tc5::sdesc(bh + off, 128, sbo), idesc, ks > 0);
+    tc5::mma_tf32(tmem, tc5::sdesc(ah + off, 128, sbo), tc5::sdesc(bl + off, 128, sbo), idesc, 1);
+    tc5::mma_tf32(tmem, tc5::sdesc(ah + off, 128, sbo), tc5::sdesc(bh + off, 128, sbo), idesc, 1);
   }
-  {
-    const int r0 = 16 * warp + g;
-#pragma unroll
-    for (int n = 0; n < kTcMaxNt; ++n) {
-      if (n < ntc) {
-        const int c = 8 * n + 2 * t4;
+}
+
+// asynchronous 4-byte global -> shared copy; zero-fills when !valid (src unread)
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(tc5::smem_u32(dst)), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+
+constexpr int kUmmaThreads = 256;   // 8 warps: warps w and w + 4 share accumulator lanes 32 (w % 4) ..
+
+__device__ __forceinline__ float4 split4(float4& v) {   // v -> lo parts, returns hi parts
+  float4 h;
+  h.x = __uint_as_float(tf32_rna(v.x)); v.x = __uint_as_float(tf32_rna(v.x - h.x));
+  h.y = __uint_as_float(tf32_rna(v.y)); v.y = __uint_as_float(tf32_rna(v.y - h.y));
+  h.z = __uint_as_float(tf32_rna(v.z)); v.z = __uint_as_float(tf32_rna(v.z - h.z));
+  h.w = __uint_as_float(tf32_rna(v.w)); v.w = __uint_as_float(tf32_rna(v.w - h.w));
+  return h;
+}
+
+// Both 1-D transforms of the (ny x nx) plane k = blockIdx.x for the columns
+// [a0, a0 + Na) of chunk blockIdx.y (Na a multiple of 16, <= 128):
+//   GEMM 1 (transposed):  T^T[a][j] = sum_i M1[a0 + a][i] in[k][j][i]
+//                         M = 128 (a), N = N1 = up16(ny) (j), K = up8(nx) (i)
+//   GEMM 2:               out[k][b][a0 + a] = sum_j M2[b][j] T^T[a][j]
+//                         M = 128 (b), N = Na (a), K = up8(ny) (j)
+// The plane is copied with cp.async straight into its canonical positions
+// (16-byte runs of 4 columns; vec: nx % 4 == 0 so that every full run is
+// 16-byte aligned in global memory) and split in place by the thread that
+// copied it.  256 threads; warps w and w + 4 own accumulator rows
+// 32 (w % 4) .. + 31, the first and second half of the columns.
+__global__ void __launch_bounds__(kUmmaThreads) k_slab_umma(const float* __restrict__ in,
+                                                            float* __restrict__ out,
+                                                            const float* __restrict__ bx,
+                                                            const float* __restrict__ ay, int nx, int ny,
+                                                            int Na, uint32_t tcols, int vec) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int K1 = up8(nx), K2 = up8(ny), Km = K1 > K2 ? K1 : K2;
+  const int N1 = up16(ny), Nb = N1 > Na ? N1 : Na;
+  float* Ah = reinterpret_cast<float*>(sm);
+  float* Al = Ah + 128 * Km;
+  float* Bh = Al + 128 * Km;
+  float* Bl = Bh + Nb * Km;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int k = blockIdx.x, a0 = blockIdx.y * Na;
+  if (warp == 0) tc5::tmem_alloc(&tslot, tcols);
+  if (tid == 0) tc5::mbar_init(&bar, 1);
+  // M1 chunk [hi | lo] (128 x K1) -> region A
+  stage_pair(bx + (size_t)blockIdx.y * 2 * 128 * K1, Ah, Al, 128 * K1, tid, kUmmaThreads);
+  // the plane (N1 x K1: rows j, columns i) -> Bl in canonical order; a warp
+  // pass covers 8 rows x 4 runs (lane: row 8 rb + lane % 8, run 4 kq + lane / 8)
+  const float* ink = in + (size_t)k * nx * ny;
+  const int kb4 = K1 >> 2, kq4 = (kb4 + 3) >> 2;
+  const int sbo1 = kb4 * 32;   // floats per 8-row block
+  for (int t = warp; t < (N1 >> 3) * kq4; t += 8) {
+    const int rb = t / kq4, kq = t - rb * kq4;
+    const int j = 8 * rb + (lane & 7), kb = 4 * kq + (lane >> 3);
+    if (kb < kb4) {
+      float* dst = Bl + rb * sbo1 + kb * 32 + (lane & 7) * 4;
+      const int i0 = 4 * kb;
+      if (vec && j < ny && i0 + 3 < nx) {
+        tc5::cp_async16(dst, ink + j * nx + i0);
+      } else {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int o = (r0 + 8 * (q >> 1)) * ldT + c + (q & 1);
-          uint32_t h, l;
-          split_tf32(acc[n][q], h, l);
-          Th[o] = __uint_as_float(h);
-          Tl[o] = __uint_as_float(l);
+          const bool ok = j < ny && i0 + q < nx;
+          cp_async4(dst + q, ok ? ink + j * nx + i0 + q : ink, ok);
         }
       }
     }
   }
+  tc5::cp_async_wait_all();
+  for (int t = warp; t < (N1 >> 3) * kq4; t += 8) {
+    const int rb = t / kq4, kq = t - rb * kq4;
+    const int kb = 4 * kq + (lane >> 3);
+    if (kb < kb4) {
+      const int o = rb * sbo1 + kb * 32 + (lane & 7) * 4;
+      float4 v = *reinterpret_cast<float4*>(Bl + o);
+      const float4 h = split4(v);
+      *reinterpret_cast<float4*>(Bh + o) = h;
+      *reinterpret_cast<float4*>(Bl + o) = v;
+    }
+  }
+  tc5::fence_proxy_async();
+  tc5::fence_before_sync();
   __syncthreads();
-
-#pragma unroll
-  for (int n = 0; n < kTcMaxNt; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  const float4* aw = ay + (size_t)warp * KS2 * 64 + 2 * lane;
-  float4 h4n = __ldg(aw), l4n = __ldg(aw + 1);
-  for (int ks = 0; ks < KS2; ++ks) {
-    const float4 h4 = h4n, l4 = l4n;
-    if (ks + 1 < KS2) {
-      h4n = __ldg(aw + (ks + 1) * 64);
-      l4n = __ldg(aw + (ks + 1) * 64 + 1);
-    }
-    const uint32_t ah[4] = {f2u(h4.x), f2u(h4.y), f2u(h4.z), f2u(h4.w)};
-    const uint32_t al[4] = {f2u(l4.x), f2u(l4.y), f2u(l4.z), f2u(l4.w)};
-    const int o = (8 * ks + t4) * ldT + g;
-    uint32_t bh[kTcMaxNt][2], bl[kTcMaxNt][2];
-#pragma unroll
-    for (int n = 0; n < kTcMaxNt; ++n)
-      if (n < ntc) {
-        const int on = o + 8 * n;
-        bh[n][0] = f2u(Th[on]);
-        bh[n][1] = f2u(Th[on + 4 * ldT]);
-        bl[n][0] = f2u(Tl[on]);
-        bl[n][1] = f2u(Tl[on + 4 * ldT]);
-      }
-#pragma unroll
-    for (int n = 0; n < kTcMaxNt; ++n)
-      if (n < ntc) mma_tf32(acc[n], al, bh[n][0], bh[n][1]);
-#pragma unroll
-    for (int n = 0; n < kTcMaxNt; ++n)
-      if (n < ntc) mma_tf32(acc[n], ah, bl[n][0], bl[n][1]);
-#pragma unroll
-    for (int n = 0; n < kTcMaxNt; ++n)
-      if (n < ntc) mma_tf32(acc[n], ah, bh[n][0], bh[n][1]);
+  tc5::fence_after_sync();
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    issue_split_gemm(tmem, Ah, Al, Bh, Bl, K1, N1);
+    tc5::commit(&bar);
   }
-  float* outk = out + (int64_t)blockIdx.x * nx * ny;
-  const int b0 = 16 * warp + g;
-#pragma unroll
-  for (int n = 0; n < kTcMaxNt; ++n) {
-    if (n < ntc) {
-      const int a = a0 + 8 * n + 2 * t4;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int b = b0 + 8 * (q >> 1), aa = a + (q & 1);
-        if (b < ny && aa < nx) outk[b * nx + aa] = acc[n][q];
+  const bool ok1 = tc5::mbar_wait(&bar, 0, kMbarLimit);
+  __syncwarp();   // tcgen05.ld is warp-collective
+  tc5::fence_after_sync();
+  // region A is free: stage M2 while T^T moves from tensor memory to region B
+  stage_pair(ay, Ah, Al, 128 * K2, tid, kUmmaThreads);
+  const int row = 32 * (warp & 3) + lane;
+  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  {
+    const int half = ((N1 >> 3) + 1) >> 1;   // 8-column chunks of the first half
+    const int c_begin = warp < 4 ? 0 : 8 * half, c_end = warp < 4 ? 8 * half : N1;
+    for (int c = c_begin; c < c_end; c += 8) {
+      float v[8];
+      tc5::ld8(trow + (uint32_t)c, v);
+      if (row < Na && c < K2) {
+        float4 lo0 = make_float4(v[0], v[1], v[2], v[3]), lo1 = make_float4(v[4], v[5], v[6], v[7]);
+        if (!ok1) lo0 = lo1 = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+        const float4 hi0 = split4(lo0), hi1 = split4(lo1);
+        const uint32_t o = tc5::canon_offset(row, c, K2) >> 2;
+        *reinterpret_cast<float4*>(Bh + o) = hi0;
+        *reinterpret_cast<float4*>(Bh + o + 32) = hi1;
+        *reinterpret_cast<float4*>(Bl + o) = lo0;
+        *reinterpret_cast<float4*>(Bl + o + 32) = lo1;
       }
     }
   }
+  tc5::cp_async_wait_all();
+  tc5::fence_proxy_async();
+  tc5::fence_before_sync();
+  __syncthreads();
+  tc5::fence_after_sync();
+  if (tid == 0) {
+    issue_split_gemm(tmem, Ah, Al, Bh, Bl, K2, Na);
+    tc5::commit(&bar);
+  }
+  const bool ok2 = tc5::mbar_wait(&bar, 1, kMbarLimit);
+  __syncwarp();
+  tc5::fence_after_sync();
+  {
+    float* outr = out + (size_t)k * nx * ny + (size_t)row * nx;
+    const int half = ((Na >> 3) + 1) >> 1;
+    const int c_begin = warp < 4 ? 0 : 8 * half, c_end = warp < 4 ? 8 * half : Na;
+    for (int c = c_begin; c < c_end; c += 8) {
+      float v[8];
+      tc5::ld8(trow + (uint32_t)c, v);
+      if (!ok2) v[0] = __int_as_float(0x7fc00000);
+      const int a = a0 + c;
+      if (row < ny) {
+        if (vec && a + 7 < nx) {
+          *reinterpret_cast<float4*>(outr + a) = make_float4(v[0], v[1], v[2], v[3]);
+          *reinterpret_cast<float4*>(outr + a + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (a + q < nx) outr[a + q] = v[q];
+        }
+      }
+    }
+  }
+  tc5::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc5::tmem_dealloc(tmem, tcols);
 }
 
-// z-direction forward transform, eigenvalue scaling and inverse transform of
-// kTcCols (x, y) columns q0 + [0, kTcCols), q = j nx + i:
-//   t[c][q] = sum_k Ez^-1[c][k] in[k][q] / (lam_z[c] + lam_y[j] + lam_x[i])   (null mode -> 0)
+// z transform, eigenvalue scaling and inverse z transform of the N (x, y)
+// columns q0 + [0, N), q = j nx + i:
+//   t[c][q] = sum_k Ez^-1[c][k] in[k][q] / (lam_z[c] + lam_y[j] + lam_x[i])  (null mode -> 0)
 //   out[m][q] = sum_c Ez[m][c] t[c][q]
-// One warp per 16-row tile (blockDim = 32 * up16(nz) / 16).  Shared memory:
-// X hi / lo [16 MT][ldX] (input, then t), lam_x + lam_y and the null flag per column.
-__global__ void __launch_bounds__(256) k_col_z_tc(const float* __restrict__ in,
-                                                  float* __restrict__ out, TpfDev<float> tp,
-                                                  const float4* __restrict__ azi,
-                                                  const float4* __restrict__ aze, int ldX) {
-  extern __shared__ __align__(16) float sm[];
+// GEMM 1: A = Ez^-1, B = in^T; GEMM 2: A = Ez, B = t^T.  256 threads (as above).
+// vec: Q % 4 == 0 and N % 4 == 0 (16-byte aligned output runs).
+__global__ void __launch_bounds__(kUmmaThreads) k_col_umma(const float* __restrict__ in,
+                                                           float* __restrict__ out, TpfDev<float> tp,
+                                                           const float* __restrict__ azi,
+                                                           const float* __restrict__ aze, int N,
+                                                           uint32_t tcols, int vec) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
   const int nx = tp.n[0], ny = tp.n[1], nz = tp.n[2];
-  const int MT = blockDim.x >> 5, KS = up8(nz) >> 3;
-  const int64_t Q = (int64_t)nx * ny;
-  const int64_t q0 = (int64_t)blockIdx.x * kTcCols;
-  float* Xh = sm;
-  float* Xl = Xh + 16 * MT * ldX;
-  float* lamq = Xl + 16 * MT * ldX;
-  int* nullq = reinterpret_cast<int*>(lamq + kTcCols);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
-  for (int k = warp; k < 16 * MT; k += MT)
-    for (int q = lane; q < kTcCols; q += 32) {
-      const bool ok = k < nz && q0 + q < Q;
-      cp_async4(Xh + k * ldX + q, ok ? in + k * Q + q0 + q : in, ok);
+  const int Kz = up8(nz);
+  const int64_t Q = (int64_t)nx * ny, q0 = (int64_t)blockIdx.x * N;
+  float* Ah = reinterpret_cast<float*>(sm);
+  float* Al = Ah + 128 * Kz;
+  float* Bh = Al + 128 * Kz;
+  float* Bl = Bh + N * Kz;
+  float* lamq = Bl + N * Kz;
+  int* nullq = reinterpret_cast<int*>(lamq + N);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc5::tmem_alloc(&tslot, tcols);
+  if (tid == 0) tc5::mbar_init(&bar, 1);
+  stage_pair(azi, Ah, Al, 128 * Kz, tid, kUmmaThreads);
+  // in^T (rows q, columns kk) -> Bl at its canonical positions; lanes run
+  // along q (consecutive addresses in global memory)
+  for (int kk = warp; kk < Kz; kk += 8)
+    for (int q = lane; q < N; q += 32) {
+      const bool ok = kk < nz && q0 + q < Q;
+      cp_async4(Bl + (tc5::canon_offset(q, kk, Kz) >> 2), ok ? in + kk * Q + q0 + q : in, ok);
     }
-  for (int q = tid; q < kTcCols; q += blockDim.x) {
+  for (int q = tid; q < N; q += kUmmaThreads) {
     const int64_t qq = q0 + q;
     float lq = 1.f;
     int nl = 0;
@@ -547,157 +582,111 @@ __global__ void __launch_bounds__(256) k_col_z_tc(const float* __restrict__ in,
     lamq[q] = lq;
     nullq[q] = nl;
   }
-  cp_async_wait_all();
-  // each thread splits the elements it copied (same indices as the copy loop)
-  for (int k = warp; k < 16 * MT; k += MT)
-    for (int q = lane; q < kTcCols; q += 32) {
-      uint32_t h, l;
-      split_tf32(Xh[k * ldX + q], h, l);
-      Xh[k * ldX + q] = __uint_as_float(h);
-      Xl[k * ldX + q] = __uint_as_float(l);
+  tc5::cp_async_wait_all();
+  for (int kk = warp; kk < Kz; kk += 8)
+    for (int q = lane; q < N; q += 32) {
+      const uint32_t o = tc5::canon_offset(q, kk, Kz) >> 2;
+      split_store(Bl[o], Bh + o, Bl + o);
     }
+  tc5::fence_proxy_async();
+  tc5::fence_before_sync();
   __syncthreads();
-
-  constexpr int NT = kTcCols / 8;
-  float acc[NT][4];
-#pragma unroll
-  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  const float4* aw = azi + (size_t)warp * KS * 64 + 2 * lane;
-  float4 h4n = __ldg(aw), l4n = __ldg(aw + 1);
-  for (int ks = 0; ks < KS; ++ks) {
-    const float4 h4 = h4n, l4 = l4n;
-    if (ks + 1 < KS) {
-      h4n = __ldg(aw + (ks + 1) * 64);
-      l4n = __ldg(aw + (ks + 1) * 64 + 1);
-    }
-    const uint32_t ah[4] = {f2u(h4.x), f2u(h4.y), f2u(h4.z), f2u(h4.w)};
-    const uint32_t al[4] = {f2u(l4.x), f2u(l4.y), f2u(l4.z), f2u(l4.w)};
-    const int o = (8 * ks + t4) * ldX + g;
-    uint32_t bh[NT][2], bl[NT][2];
-#pragma unroll
-    for (int n = 0; n < NT; ++n) {
-      const int on = o + 8 * n;
-      bh[n][0] = f2u(Xh[on]);
-      bh[n][1] = f2u(Xh[on + 4 * ldX]);
-      bl[n][0] = f2u(Xl[on]);
-      bl[n][1] = f2u(Xl[on + 4 * ldX]);
-    }
-#pragma unroll
-    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], al, bh[n][0], bh[n][1]);
-#pragma unroll
-    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], ah, bl[n][0], bl[n][1]);
-#pragma unroll
-    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], ah, bh[n][0], bh[n][1]);
+  tc5::fence_after_sync();
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    issue_split_gemm(tmem, Ah, Al, Bh, Bl, Kz, N);
+    tc5::commit(&bar);
   }
-  __syncthreads();   // every warp is done reading X: t overwrites it
+  const bool ok1 = tc5::mbar_wait(&bar, 0, kMbarLimit);
+  __syncwarp();   // tcgen05.ld is warp-collective
+  tc5::fence_after_sync();
+  stage_pair(aze, Ah, Al, 128 * Kz, tid, kUmmaThreads);
+  const int row = 32 * (warp & 3) + lane;   // c of GEMM 1, m of GEMM 2
+  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  const int half = ((N >> 3) + 1) >> 1;
+  const int c_begin = warp < 4 ? 0 : 8 * half, c_end = warp < 4 ? 8 * half : N;
   {
-    const int c0 = 16 * warp + g;
+    const float lz = row < nz ? tp.lam[2][row] : 1.f;
+    const bool nullrow = row == tp.null_index[2];
+    for (int c = c_begin; c < c_end; c += 8) {
+      float v[8];
+      tc5::ld8(trow + (uint32_t)c, v);
+      if (row < Kz) {
 #pragma unroll
-    for (int n = 0; n < NT; ++n) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c = c0 + 8 * (q >> 1), col = 8 * n + 2 * t4 + (q & 1);
-        float v = 0.f;
-        if (c < nz && q0 + col < Q && !(c == tp.null_index[2] && nullq[col]))
-          v = acc[n][q] / (tp.lam[2][c] + lamq[col]);
-        uint32_t h, l;
-        split_tf32(v, h, l);
-        Xh[c * ldX + col] = __uint_as_float(h);
-        Xl[c * ldX + col] = __uint_as_float(l);
+        for (int q = 0; q < 8; ++q) {
+          const int col = c + q;
+          float t = 0.f;
+          if (row < nz && q0 + col < Q && !(nullrow && nullq[col])) t = v[q] / (lz + lamq[col]);
+          if (!ok1) t = __int_as_float(0x7fc00000);
+          const uint32_t o = tc5::canon_offset(col, row, Kz) >> 2;
+          split_store(t, Bh + o, Bl + o);
+        }
       }
     }
   }
+  tc5::cp_async_wait_all();
+  tc5::fence_proxy_async();
+  tc5::fence_before_sync();
   __syncthreads();
-
-#pragma unroll
-  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  aw = aze + (size_t)warp * KS * 64 + 2 * lane;
-  h4n = __ldg(aw);
-  l4n = __ldg(aw + 1);
-  for (int ks = 0; ks < KS; ++ks) {
-    const float4 h4 = h4n, l4 = l4n;
-    if (ks + 1 < KS) {
-      h4n = __ldg(aw + (ks + 1) * 64);
-      l4n = __ldg(aw + (ks + 1) * 64 + 1);
-    }
-    const uint32_t ah[4] = {f2u(h4.x), f2u(h4.y), f2u(h4.z), f2u(h4.w)};
-    const uint32_t al[4] = {f2u(l4.x), f2u(l4.y), f2u(l4.z), f2u(l4.w)};
-    const int o = (8 * ks + t4) * ldX + g;
-    uint32_t bh[NT][2], bl[NT][2];
-#pragma unroll
-    for (int n = 0; n < NT; ++n) {
-      const int on = o + 8 * n;
-      bh[n][0] = f2u(Xh[on]);
-      bh[n][1] = f2u(Xh[on + 4 * ldX]);
-      bl[n][0] = f2u(Xl[on]);
-      bl[n][1] = f2u(Xl[on + 4 * ldX]);
-    }
-#pragma unroll
-    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], al, bh[n][0], bh[n][1]);
-#pragma unroll
-    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], ah, bl[n][0], bl[n][1]);
-#pragma unroll
-    for (int n = 0; n < NT; ++n) mma_tf32(acc[n], ah, bh[n][0], bh[n][1]);
+  tc5::fence_after_sync();
+  if (tid == 0) {
+    issue_split_gemm(tmem, Ah, Al, Bh, Bl, Kz, N);
+    tc5::commit(&bar);
   }
-  const int m0 = 16 * warp + g;
+  const bool ok2 = tc5::mbar_wait(&bar, 1, kMbarLimit);
+  __syncwarp();
+  tc5::fence_after_sync();
+  for (int c = c_begin; c < c_end; c += 8) {
+    float v[8];
+    tc5::ld8(trow + (uint32_t)c, v);
+    if (!ok2) v[0] = __int_as_float(0x7fc00000);
+    if (row < nz) {
+      float* o = out + row * Q + q0 + c;
+      if (vec && q0 + c + 7 < Q) {
+        *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4*>(o + 4) = make_float4(v[4], v[5], v[6], v[7]);
+      } else {
 #pragma unroll
-  for (int n = 0; n < NT; ++n) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int m = m0 + 8 * (q >> 1);
-      const int64_t col = q0 + 8 * n + 2 * t4 + (q & 1);
-      if (m < nz && col < Q) out[m * Q + col] = acc[n][q];
+        for (int q = 0; q < 8; ++q)
+          if (q0 + c + q < Q) o[q] = v[q];
+      }
     }
   }
+  tc5::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc5::tmem_dealloc(tmem, tcols);
 }
 
-// launch shapes of the fused kernels
-struct SlabShape {
-  int nsplit, ncol, ldP, ldT, threads;
-  size_t smem;
-};
-
-inline SlabShape slab_shape(int nx, int ny, int nz) {
-  SlabShape s;
-  const int kp = up8(nx);
-  // column split: at least enough for 8 n-tiles per block; among up to 4,
-  // the one whose nz * nsplit blocks fill whole waves of 2 blocks per SM best
-  const int nmin = (kp + 8 * kTcMaxNt - 1) / (8 * kTcMaxNt);
-  s.nsplit = nmin;
-  double best = -1.0;
-  for (int ns = nmin; ns <= 4 && 8 * ns <= kp; ++ns) {
-    const int64_t blocks = (int64_t)nz * ns, slots = 2 * 152;
-    const double eff = (double)blocks / (double)(((blocks + slots - 1) / slots) * slots);
-    if (eff > best + 1e-9) { best = eff; s.nsplit = ns; }
-  }
-  s.ncol = up8((kp + s.nsplit - 1) / s.nsplit);
-  s.ldP = kp + 4;                 // ldP / 4 odd: the A-fragment reads hit 32 banks
-  s.ldT = ld_b(s.ncol);
-  s.threads = 32 * (up16(ny) / 16);
-  s.smem = sizeof(float) * (size_t)up16(ny) * (s.ldP + 2 * s.ldT);
-  return s;
+inline size_t slab_smem(int nx, int ny, int Na) {
+  const int Km = up8(nx) > up8(ny) ? up8(nx) : up8(ny);
+  const int Nb = up16(ny) > Na ? up16(ny) : Na;
+  return sizeof(float) * (size_t)(2 * 128 + 2 * Nb) * Km;
 }
 
-struct ColShape {
-  int ldX, threads;
-  unsigned blocks;
-  size_t smem;
-};
+inline size_t col_smem(int nz, int N) {
+  return sizeof(float) * ((size_t)(2 * 128 + 2 * N) * up8(nz) + 2 * (size_t)N);
+}
 
-inline ColShape col_shape(int nx, int ny, int nz) {
-  ColShape c;
-  c.ldX = ld_b(kTcCols);
-  c.threads = 32 * (up16(nz) / 16);
-  c.blocks = (unsigned)(((int64_t)nx * ny + kTcCols - 1) / kTcCols);
-  c.smem = sizeof(float) * ((size_t)2 * up16(nz) * c.ldX + 2 * kTcCols);
-  return c;
+constexpr size_t kSmemCap = 220 * 1024;
+
+// launch shapes, fixed per grid: the slab kernel covers a plane's columns in
+// one chunk (up16(nx) <= 128); the column kernel takes N columns per block so
+// that its blocks cover the SMs once (N a multiple of 16, <= 128)
+inline void tc_shapes(int nx, int ny, int nz, int* nsplit, int* slab_n, int* col_n) {
+  *nsplit = 1;
+  *slab_n = up16(nx);
+  const int64_t Q = (int64_t)nx * ny;
+  int n = up16((int)((Q + 151) / 152));
+  if (n > 128) n = 128;
+  while (n > 16 && col_smem(nz, n) > kSmemCap) n -= 16;
+  *col_n = n;
 }
 
 fv_status set_tc_attributes() {
   static bool done = false;   // the attribute is per function, not per grid
   if (!done) {
-    FV_CUDA(cudaFuncSetAttribute(k_slab_xy_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    FV_CUDA(cudaFuncSetAttribute(k_col_z_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    FV_CUDA(cudaFuncSetAttribute(k_slab_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
+    FV_CUDA(cudaFuncSetAttribute(k_col_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
     done = true;
   }
   return FV_OK;
@@ -706,19 +695,21 @@ fv_status set_tc_attributes() {
 // dir 0: forward (Einv) transforms, 1: inverse (E)
 fv_status launch_slab(const fv_grid* g, const float* in, float* out, int dir) {
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-  const SlabShape s = slab_shape(nx, ny, nz);
+  const int N = g->tc.slab_n;
   LaunchScope ls_(g, FV_K_TPF_X);
-  k_slab_xy_tc<<<dim3(nz, s.nsplit), s.threads, s.smem, g->stream>>>(
-      in, out, g->tc.bx[dir], g->tc.ay[dir], nx, ny, s.ncol, s.ldP, s.ldT);
+  k_slab_umma<<<dim3(nz, g->tc.slab_nsplit), kUmmaThreads, slab_smem(nx, ny, N), g->stream>>>(
+      in, out, g->tc.bx[dir], g->tc.ay[dir], nx, ny, N, tmem_cols(up16(ny) > N ? up16(ny) : N),
+      (nx % 4 == 0 && N % 4 == 0) ? 1 : 0);
   FV_CHECK_LAUNCH();
   return FV_OK;
 }
 
 fv_status launch_col(const fv_grid* g, const float* in, float* out) {
-  const ColShape c = col_shape(g->n[0], g->n[1], g->n[2]);
+  const int N = g->tc.col_n;
+  const int64_t Q = (int64_t)g->n[0] * g->n[1];
   LaunchScope ls_(g, FV_K_TPF_YZ);
-  k_col_z_tc<<<c.blocks, c.threads, c.smem, g->stream>>>(in, out, g->tpf_f, g->tc.az[0], g->tc.az[1],
-                                                         c.ldX);
+  k_col_umma<<<(unsigned)((Q + N - 1) / N), kUmmaThreads, col_smem(g->n[2], N), g->stream>>>(
+      in, out, g->tpf_f, g->tc.az[0], g->tc.az[1], N, tmem_cols(N), (Q % 4 == 0 && N % 4 == 0) ? 1 : 0);
   FV_CHECK_LAUNCH();
   return FV_OK;
 }
@@ -762,81 +753,71 @@ static float tf32_host(float x) {
   return r;
 }
 
-static void split_host(double x, float& hi, float& lo) {
-  hi = tf32_host((float)x);
-  lo = tf32_host((float)(x - (double)hi));
+// [hi | lo] of the rows x kdim operand whose element (r, k) is f(r, k), in
+// the canonical K-major layout
+template <typename F>
+static void lay_out(int rows, int kdim, F f, float* out) {
+  const size_t half = (size_t)rows * kdim;
+  for (int r = 0; r < rows; ++r)
+    for (int k = 0; k < kdim; ++k) {
+      const double x = f(r, k);
+      const float hi = tf32_host((float)x);
+      const float lo = tf32_host((float)(x - (double)hi));
+      const size_t o = tc5::canon_offset(r, k, kdim) / 4;
+      out[o] = hi;
+      out[half + o] = lo;
+    }
 }
 
-// B fragments of M (n x n, row-major): B[k = i][col = a] = M[a][i]
-static void frag_b(const std::vector<double>& M, int n, float4* out) {
-  const int KS = up8(n) / 8;
-  for (int nt = 0; nt < KS; ++nt)
-    for (int ks = 0; ks < KS; ++ks)
-      for (int lane = 0; lane < 32; ++lane) {
-        const int g = lane >> 2, t4 = lane & 3;
-        const int a = 8 * nt + g, i0 = 8 * ks + t4, i1 = i0 + 4;
-        const double v0 = (a < n && i0 < n) ? M[(size_t)a * n + i0] : 0.0;
-        const double v1 = (a < n && i1 < n) ? M[(size_t)a * n + i1] : 0.0;
-        float h0, l0, h1, l1;
-        split_host(v0, h0, l0);
-        split_host(v1, h1, l1);
-        out[((size_t)nt * KS + ks) * 32 + lane] = make_float4(h0, h1, l0, l1);
-      }
-}
-
-// A fragments of M (n x n, row-major): A[row = r][k = c] = M[r][c]
-static void frag_a(const std::vector<double>& M, int n, float4* out) {
-  const int KS = up8(n) / 8, MT = up16(n) / 16;
-  for (int mt = 0; mt < MT; ++mt)
-    for (int ks = 0; ks < KS; ++ks)
-      for (int lane = 0; lane < 32; ++lane) {
-        const int g = lane >> 2, t4 = lane & 3;
-        const int r[4] = {16 * mt + g, 16 * mt + g + 8, 16 * mt + g, 16 * mt + g + 8};
-        const int c[4] = {8 * ks + t4, 8 * ks + t4, 8 * ks + t4 + 4, 8 * ks + t4 + 4};
-        float h[4], l[4];
-        for (int q = 0; q < 4; ++q)
-          split_host((r[q] < n && c[q] < n) ? M[(size_t)r[q] * n + c[q]] : 0.0, h[q], l[q]);
-        float4* o = out + (((size_t)mt * KS + ks) * 32 + lane) * 2;
-        o[0] = make_float4(h[0], h[1], h[2], h[3]);
-        o[1] = make_float4(l[0], l[1], l[2], l[3]);
-      }
-}
-
-fv_status build_tc_frags(fv_grid* g) {
-  g->tc = TcFrags();
+fv_status build_tc_mats(fv_grid* g) {
+  g->tc = TcMats();
   for (int d = 0; d < 3; ++d)
     if (g->n[d] > kFusedMax) return FV_OK;   // the fused kernels serve n <= 128 only
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-  const size_t szb = (size_t)(up8(nx) / 8) * (up8(nx) / 8) * 32;
-  const size_t sza_y = (size_t)(up16(ny) / 16) * (up8(ny) / 8) * 64;
-  const size_t sza_z = (size_t)(up16(nz) / 16) * (up8(nz) / 8) * 64;
-  const size_t total = 2 * (szb + sza_y + sza_z);
-  std::vector<float4> h(total);
-  float4* p = h.data();
-  float4* bx[2] = {p, p + szb};
-  float4* ay[2] = {p + 2 * szb, p + 2 * szb + sza_y};
-  float4* az[2] = {p + 2 * szb + 2 * sza_y, p + 2 * szb + 2 * sza_y + sza_z};
-  frag_b(g->basis[0].Einv, nx, bx[0]);
-  frag_b(g->basis[0].E, nx, bx[1]);
-  frag_a(g->basis[1].Einv, ny, ay[0]);
-  frag_a(g->basis[1].E, ny, ay[1]);
-  frag_a(g->basis[2].Einv, nz, az[0]);
-  frag_a(g->basis[2].E, nz, az[1]);
-  cudaError_t e = cudaMalloc(&g->d_tc, total * sizeof(float4));
+  const int K1 = up8(nx), K2 = up8(ny), Kz = up8(nz);
+  int ns, N, Nc;
+  tc_shapes(nx, ny, nz, &ns, &N, &Nc);
+  const size_t szb = (size_t)ns * 2 * 128 * K1, sza = (size_t)2 * 128 * K2, szz = (size_t)2 * 128 * Kz;
+  const size_t total = 2 * szb + 2 * sza + 2 * szz;
+  std::vector<float> h(total, 0.f);
+  float* p = h.data();
+  size_t off_bx[2], off_ay[2], off_az[2], o = 0;
+  for (int dir = 0; dir < 2; ++dir) { off_bx[dir] = o; o += szb; }
+  for (int dir = 0; dir < 2; ++dir) { off_ay[dir] = o; o += sza; }
+  for (int q = 0; q < 2; ++q) { off_az[q] = o; o += szz; }
+  for (int dir = 0; dir < 2; ++dir) {
+    const std::vector<double>& Mx = dir == 0 ? g->basis[0].Einv : g->basis[0].E;
+    const std::vector<double>& My = dir == 0 ? g->basis[1].Einv : g->basis[1].E;
+    const std::vector<double>& Mz = dir == 0 ? g->basis[2].Einv : g->basis[2].E;
+    for (int c = 0; c < ns; ++c) {
+      const int a0 = c * N;
+      lay_out(128, K1,
+              [&](int r, int k) { return (r < N && a0 + r < nx && k < nx) ? Mx[(size_t)(a0 + r) * nx + k] : 0.0; },
+              p + off_bx[dir] + (size_t)c * 2 * 128 * K1);
+    }
+    lay_out(128, K2, [&](int r, int k) { return (r < ny && k < ny) ? My[(size_t)r * ny + k] : 0.0; },
+            p + off_ay[dir]);
+    lay_out(128, Kz, [&](int r, int k) { return (r < nz && k < nz) ? Mz[(size_t)r * nz + k] : 0.0; },
+            p + off_az[dir]);
+  }
+  cudaError_t e = cudaMalloc(&g->d_tc, total * sizeof(float));
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     g->d_tc = nullptr;
-    set_error("cudaMalloc of the tensor-core fragments failed");
+    set_error("cudaMalloc of the tensor-core operands failed");
     return FV_ENOMEM;
   }
-  g->ws_bytes += (int64_t)(total * sizeof(float4));
-  FV_CUDA(cudaMemcpy(g->d_tc, h.data(), total * sizeof(float4), cudaMemcpyHostToDevice));
-  const float4* base = (const float4*)g->d_tc;
+  g->ws_bytes += (int64_t)(total * sizeof(float));
+  FV_CUDA(cudaMemcpy(g->d_tc, h.data(), total * sizeof(float), cudaMemcpyHostToDevice));
+  const float* base = (const float*)g->d_tc;
   for (int q = 0; q < 2; ++q) {
-    g->tc.bx[q] = base + (bx[q] - p);
-    g->tc.ay[q] = base + (ay[q] - p);
-    g->tc.az[q] = base + (az[q] - p);
+    g->tc.bx[q] = base + off_bx[q];
+    g->tc.ay[q] = base + off_ay[q];
+    g->tc.az[q] = base + off_az[q];
   }
+  g->tc.slab_nsplit = ns;
+  g->tc.slab_n = N;
+  g->tc.col_n = Nc;
   g->tc.ready = true;
   return FV_OK;
 }

@@ -318,7 +318,8 @@ def run_ours(args):
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured) x 1.1/2.25 "
                                    "(nominal dense TF32/BF16)",
                     "tensor_ops_tflops": 3 * achieved,
-                    "note": "mma.sync m16n8k8 TF32, a*b = a_hi b_hi + a_hi b_lo + a_lo b_hi"}
+                    "note": "tcgen05.mma kind::tf32 (TMEM accumulators), "
+                            "a*b = a_lo b_hi + a_hi b_lo + a_hi b_hi"}
         elif "flops" in alg:
             peak = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
             achieved = alg["flops"] / per_launch_s / 1e12

@@ -342,12 +342,6 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
-__device__ __forceinline__ void split_store(float x, float* hi, float* lo) {
-  const uint32_t h = tf32_rna(x);
-  *hi = __uint_as_float(h);
-  *lo = __uint_as_float(tf32_rna(x - __uint_as_float(h)));   // exact difference, rounded to TF32
-}
-
 constexpr int kMbarLimit = 1 << 22;   // polls of an mbarrier before the block gives up
 
 __host__ __device__ __forceinline__ int up16(int n) { return (n + 15) & ~15; }
@@ -541,7 +535,11 @@ __global__ void __launch_bounds__(kUmmaThreads) k_slab_umma(const float* __restr
 //   t[c][q] = sum_k Ez^-1[c][k] in[k][q] / (lam_z[c] + lam_y[j] + lam_x[i])  (null mode -> 0)
 //   out[m][q] = sum_c Ez[m][c] t[c][q]
 // GEMM 1: A = Ez^-1, B = in^T; GEMM 2: A = Ez, B = t^T.  256 threads (as above).
-// vec: Q % 4 == 0 and N % 4 == 0 (16-byte aligned output runs).
+// The input tile is copied in its own order (16-byte runs along q) into a
+// padded row-major tile R and transposed + split from there into the
+// canonical operand; the scaled intermediate goes through a per-warp 32 x 9
+// transpose scratch (in R) so that both land as 16-byte runs.
+// vec: Q % 4 == 0 and N % 4 == 0 (16-byte aligned global runs).
 __global__ void __launch_bounds__(kUmmaThreads) k_col_umma(const float* __restrict__ in,
                                                            float* __restrict__ out, TpfDev<float> tp,
                                                            const float* __restrict__ azi,
@@ -559,17 +557,31 @@ __global__ void __launch_bounds__(kUmmaThreads) k_col_umma(const float* __restri
   float* Bl = Bh + N * Kz;
   float* lamq = Bl + N * Kz;
   int* nullq = reinterpret_cast<int*>(lamq + N);
+  const int ldR = N + 4;
+  float* R = reinterpret_cast<float*>(nullq + N);   // Kz x ldR raw tile, later transpose scratch
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tc5::tmem_alloc(&tslot, tcols);
   if (tid == 0) tc5::mbar_init(&bar, 1);
   stage_pair(azi, Ah, Al, 128 * Kz, tid, kUmmaThreads);
-  // in^T (rows q, columns kk) -> Bl at its canonical positions; lanes run
-  // along q (consecutive addresses in global memory)
-  for (int kk = warp; kk < Kz; kk += 8)
-    for (int q = lane; q < N; q += 32) {
-      const bool ok = kk < nz && q0 + q < Q;
-      cp_async4(Bl + (tc5::canon_offset(q, kk, Kz) >> 2), ok ? in + kk * Q + q0 + q : in, ok);
+  // the tile in[kk][q0 .. q0 + N) -> R in 16-byte runs (rows kk >= nz and
+  // columns beyond Q zero-filled)
+  {
+    const int n4 = N >> 2;
+    for (int e = tid; e < Kz * n4; e += kUmmaThreads) {
+      const int kk = e / n4, j4 = e - kk * n4;
+      float* dst = R + kk * ldR + 4 * j4;
+      const int64_t qq = q0 + 4 * j4;
+      if (vec && kk < nz && qq + 3 < Q) {
+        tc5::cp_async16(dst, in + kk * Q + qq);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const bool ok = kk < nz && qq + i < Q;
+          cp_async4(dst + i, ok ? in + kk * Q + qq + i : in, ok);
+        }
+      }
     }
+  }
   for (int q = tid; q < N; q += kUmmaThreads) {
     const int64_t qq = q0 + q;
     float lq = 1.f;
@@ -583,11 +595,23 @@ __global__ void __launch_bounds__(kUmmaThreads) k_col_umma(const float* __restri
     nullq[q] = nl;
   }
   tc5::cp_async_wait_all();
-  for (int kk = warp; kk < Kz; kk += 8)
-    for (int q = lane; q < N; q += 32) {
-      const uint32_t o = tc5::canon_offset(q, kk, Kz) >> 2;
-      split_store(Bl[o], Bh + o, Bl + o);
+  __syncthreads();
+  // transpose + split: run (q, kb) = R[4 kb .. 4 kb + 3][q] -> canonical (q, 4 kb);
+  // a warp covers 8 consecutive q x 4 consecutive kb (512 contiguous bytes)
+  {
+    const int kb4 = Kz >> 2;
+    for (int e = tid; e < N * kb4; e += kUmmaThreads) {
+      const int ql = e & 7, rest = e >> 3;
+      const int qh = rest / kb4, kb = rest - qh * kb4;
+      const int q = 8 * qh + ql;
+      const float* rp = R + 4 * kb * ldR + q;
+      float4 v = make_float4(rp[0], rp[ldR], rp[2 * ldR], rp[3 * ldR]);
+      const float4 h = split4(v);
+      const uint32_t o = tc5::canon_offset(q, 4 * kb, Kz) >> 2;
+      *reinterpret_cast<float4*>(Bh + o) = h;
+      *reinterpret_cast<float4*>(Bl + o) = v;
     }
+  }
   tc5::fence_proxy_async();
   tc5::fence_before_sync();
   __syncthreads();
@@ -608,20 +632,35 @@ __global__ void __launch_bounds__(kUmmaThreads) k_col_umma(const float* __restri
   {
     const float lz = row < nz ? tp.lam[2][row] : 1.f;
     const bool nullrow = row == tp.null_index[2];
+    float* scr = R + warp * (32 * 9);   // this warp's 32 x 8 block, row pitch 9
+    const int ql = lane & 7, rg = lane >> 3;
     for (int c = c_begin; c < c_end; c += 8) {
       float v[8];
       tc5::ld8(trow + (uint32_t)c, v);
-      if (row < Kz) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int col = c + q;
-          float t = 0.f;
-          if (row < nz && q0 + col < Q && !(nullrow && nullq[col])) t = v[q] / (lz + lamq[col]);
-          if (!ok1) t = __int_as_float(0x7fc00000);
-          const uint32_t o = tc5::canon_offset(col, row, Kz) >> 2;
-          split_store(t, Bh + o, Bl + o);
+      for (int q = 0; q < 8; ++q) {
+        const int col = c + q;
+        float t = 0.f;
+        if (row < nz && q0 + col < Q && !(nullrow && nullq[col])) t = v[q] / (lz + lamq[col]);
+        if (!ok1) t = __int_as_float(0x7fc00000);
+        scr[lane * 9 + q] = t;
+      }
+      __syncwarp();
+      // lane: column c + ql, rows 4 rg .. 4 rg + 3 and 4 (rg + 4) .. + 3 of the warp's 32
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int r0 = 4 * (rg + 4 * hh);
+        const int grow = 32 * (warp & 3) + r0;
+        if (grow < Kz) {
+          float4 t4 = make_float4(scr[r0 * 9 + ql], scr[(r0 + 1) * 9 + ql], scr[(r0 + 2) * 9 + ql],
+                                  scr[(r0 + 3) * 9 + ql]);
+          const float4 h4 = split4(t4);
+          const uint32_t o = tc5::canon_offset(c + ql, grow, Kz) >> 2;
+          *reinterpret_cast<float4*>(Bh + o) = h4;
+          *reinterpret_cast<float4*>(Bl + o) = t4;
         }
       }
+      __syncwarp();
     }
   }
   tc5::cp_async_wait_all();
@@ -664,7 +703,9 @@ inline size_t slab_smem(int nx, int ny, int Na) {
 }
 
 inline size_t col_smem(int nz, int N) {
-  return sizeof(float) * ((size_t)(2 * 128 + 2 * N) * up8(nz) + 2 * (size_t)N);
+  // eigenbasis hi / lo, operand hi / lo, lam / null per column, raw tile R (>= 8 x 32 x 9 scratch)
+  const size_t R = (size_t)up8(nz) * (N + 4) > 8 * 32 * 9 ? (size_t)up8(nz) * (N + 4) : 8 * 32 * 9;
+  return sizeof(float) * ((size_t)(2 * 128 + 2 * N) * up8(nz) + 2 * (size_t)N + R);
 }
 
 constexpr size_t kSmemCap = 220 * 1024;

@@ -813,11 +813,15 @@ static void lay_out(int rows, int kdim, F f, float* out) {
 fv_status build_tc_mats(fv_grid* g) {
   g->tc = TcMats();
   for (int d = 0; d < 3; ++d)
-    if (g->n[d] > kFusedMax) return FV_OK;   // the fused kernels serve n <= 128 only
+    if (g->n[d] > kFusedMax) return FV_OK;   // the fused kernels serve n <= 128 at most
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   const int K1 = up8(nx), K2 = up8(ny), Kz = up8(nz);
   int ns, N, Nc;
   tc_shapes(nx, ny, nz, &ns, &N, &Nc);
+  // the plane operand (up16(ny) x up8(nx)) and the eigenbasis (128 rows) must
+  // fit one block's shared memory together (n up to about 112); larger grids
+  // take the unfused transforms
+  if (slab_smem(nx, ny, N) > kSmemCap || col_smem(nz, Nc) > kSmemCap) return FV_OK;
   const size_t szb = (size_t)ns * 2 * 128 * K1, sza = (size_t)2 * 128 * K2, szz = (size_t)2 * 128 * Kz;
   const size_t total = 2 * szb + 2 * sza + 2 * szz;
   std::vector<float> h(total, 0.f);

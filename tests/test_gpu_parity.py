@@ -94,6 +94,20 @@ def test_pressure_solve(fv, nz, ny, nx, kind):
     assert relerr(host(phi), ref) < 1e-4
 
 
+# the largest planes the fused tensor-core transforms take (112 x 112), and a
+# plane just beyond (x = 120: shared memory too small), which falls back to the
+# unfused transforms
+@pytest.mark.parametrize("nz,ny,nx", [(8, 112, 112), (16, 24, 120)])
+def test_simple_krylov_vector_fused_limits(fv, nz, ny, nx):
+    g, G, shape, U, v = setup(fv, nz, ny, nx, "cosine")
+    ref_v, _ = simple.krylov_vector(G, poisson.TPF(G), layout.to_oracle(U, shape),
+                                    layout.to_oracle(v, shape), 700.0)
+    out = torch.empty(g.n_vel, dtype=torch.float64, device="cuda")
+    st = fv.simple_krylov_solve(g, dev(U), dev(v), out, None, eps=1e-12, prec="mixed")
+    assert relerr(host(out), layout.from_oracle(ref_v)) < 2e-5
+    assert st["passes"] <= 4
+
+
 @pytest.mark.parametrize("nz,ny,nx,kind", SHAPES)
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
 def test_simple_krylov_vector(fv, nz, ny, nx, kind, prec):

@@ -93,8 +93,9 @@ __global__ void __launch_bounds__(256) k_correct_g(MetFF m, const float* __restr
                                                    const LoopState* __restrict__ ls,
                                                    float* __restrict__ part) {
   const int done = FIRST ? 0 : ls->pass;
-  const float2* vin = (done & 1) ? vff0 : vff1;   // result of pass `done` is in vff[(done-1)&1]
-  float2* vout = (done & 1) ? vff1 : vff0;
+  // result of pass `done` is in vff[(done-1)&1]; the two buffers never overlap
+  const float2* __restrict__ vin = (done & 1) ? vff0 : vff1;
+  float2* __restrict__ vout = (done & 1) ? vff1 : vff0;
   const float omega = cb->omega;
   const int plane_ = m.n[0] * m.n[1];
   const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(256) k_correct_g(MetFF m, const float* __restr
   const int i = act_ ? t_ % m.n[0] : 0;
   const int j = act_ ? t_ / m.n[0] : 0;
   float aphi = 0.f, adiv = 0.f;
+#pragma unroll
   for (int kk = 0; kk < kCellKz; ++kk) {
     const int k = blockIdx.y * kCellKz + kk;
     if (!act_ || k >= m.n[2]) continue;

@@ -362,6 +362,18 @@ def run_ours(args):
             roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peak,
                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(kind),
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    # whole-solve HBM roofline: algorithmic bytes of one evaluation (per cell:
+    # rounding U and x 72, J.v 36, D w 16, per pass 3 transform launches x 8
+    # plus the correction 72, join of v and p 64) over the time per solve
+    solve_roof = None
+    if mixed and n <= 128:
+        bpc = 72 + 36 + 16 + passes * (3 * 8 + 72) + 64
+        bytes_solve = bpc * n ** 3
+        ach = bytes_solve * value / ws / 1e9
+        pk_hbm = pk.get("hbm_gbs", 6800.0)
+        solve_roof = {"bound": "hbm", "bytes_per_solve": bytes_solve, "bytes_per_cell": bpc,
+                      "achieved": ach, "peak": pk_hbm, "unit": "GB/s", "frac": ach / pk_hbm,
+                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     step_ms = ms_max / args.steps
     # bytes moved per step
     h2d = g.n_vel * 8
@@ -386,6 +398,7 @@ def run_ours(args):
         "gpu_launches": gpu_launches,
         "kernels_per_solve": kernels_per_solve,
         "roofline": roof,
+        "solve_roofline": solve_roof,
         "kernel_breakdown": breakdown,
         "clocks": clocks,
     }

@@ -106,13 +106,27 @@ typedef struct {
   int prec;          /* fv_prec of the Krylov vectors           [FV_FP64 = 0] */
   double sigma;      /* shift of the gradient complement                 [10] */
   double simple_eps; /* SIMPLE tolerance inside GMRES                  [1e-10] */
+  int linear;        /* fv_linear: solver of each Newton correction
+                        [FV_LIN_GMRES_BICGSTAB = 0] */
+  double gmres_sat;  /* a GMRES(m) restart cycle whose residual W-norm ends
+                        above gmres_sat x its start counts as saturated [0.5] */
 } fv_newton_opts;
+
+/* Section 3: the Newton corrections are computed by restarted GMRES or by
+ * BiCGstab(2) (Sleijpen & Fokkema 1993); when GMRES(100) saturates, its last
+ * approximation is the initial guess of BiCGstab(2). */
+typedef enum {
+  FV_LIN_GMRES_BICGSTAB = 0,  /* GMRES(m) cycles until saturated, then BiCGstab(2) */
+  FV_LIN_GMRES = 1,           /* GMRES(m) only                                     */
+  FV_LIN_BICGSTAB = 2         /* BiCGstab(2) only, from a zero correction           */
+} fv_linear;
 
 typedef struct {
   int iterations;          /* Newton steps taken                        */
   int gmres_total;         /* GMRES iterations summed over all steps    */
   double res_hist[64];     /* ||F||_inf before each step (first 64)     */
   double res_final;
+  int bicgstab_total;      /* BiCGstab(2) operator applications, summed */
 } fv_newton_stats;
 
 typedef struct {
@@ -171,9 +185,12 @@ fv_status simple_krylov_solve(const fv_grid* g, const double* U, const double* v
 
 /* Section 3, Newton steps 1-4 at the grid's current Re: U[n_vel] (in: guess,
  * e.g. all zeros = rest; out: steady state) and P[n_cell] (out).  Each
- * correction solves P L_U u = P F_mom by restarted GMRES(m) whose Krylov
- * vectors come from simple_krylov_solve.  Returns FV_ENOCONV if
- * ||F||_inf >= tol after max_newton steps. */
+ * correction solves P L_U u = P F_mom (in the shifted form A_sigma) by the
+ * opts.linear solver -- restarted GMRES(m), BiCGstab(2), or GMRES(m) until
+ * it saturates followed by BiCGstab(2) -- whose operator applications come
+ * from simple_krylov_solve.  gmres_max_it caps the operator applications of
+ * both solvers per correction.  Returns FV_ENOCONV if ||F||_inf >= tol after
+ * max_newton steps. */
 fv_status newton_steady(fv_grid* g, double* U, double* P,
                         const fv_newton_opts* opts, fv_newton_stats* stats);
 

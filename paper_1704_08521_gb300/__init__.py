@@ -42,12 +42,17 @@ class fv_newton_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_newton", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("gmres_max_it", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
                 ("prec", ctypes.c_int), ("sigma", ctypes.c_double),
-                ("simple_eps", ctypes.c_double)]
+                ("simple_eps", ctypes.c_double), ("linear", ctypes.c_int),
+                ("gmres_sat", ctypes.c_double)]
 
 
 class fv_newton_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("gmres_total", ctypes.c_int),
-                ("res_hist", ctypes.c_double * 64), ("res_final", ctypes.c_double)]
+                ("res_hist", ctypes.c_double * 64), ("res_final", ctypes.c_double),
+                ("bicgstab_total", ctypes.c_int)]
+
+
+LINEAR = {"gmres+bicgstab": 0, "gmres": 1, "bicgstab": 2}
 
 
 class fv_arnoldi_opts(ctypes.Structure):
@@ -150,13 +155,15 @@ def simple_krylov_solve(g, U, v_in, v_out, p_out=None, eps=1e-8, max_pass=200, p
 
 
 def newton_steady(g, U, P, tol=1e-10, max_newton=30, gmres_m=100, gmres_max_it=20000,
-                  gmres_rtol=1e-8, prec="fp64", sigma=10.0, simple_eps=1e-10, raise_on_fail=True):
+                  gmres_rtol=1e-8, prec="fp64", sigma=10.0, simple_eps=1e-10, raise_on_fail=True,
+                  linear="gmres+bicgstab", gmres_sat=0.5):
     o = fv_newton_opts(tol, max_newton, gmres_m, gmres_max_it, gmres_rtol, PRECS.get(prec, prec),
-                       sigma, simple_eps)
+                       sigma, simple_eps, LINEAR.get(linear, linear), gmres_sat)
     s = fv_newton_stats()
     st = lib.newton_steady(g.handle, _f64(U, g.n_vel, "U"), _f64(P, g.n_cell, "P"),
                            ctypes.byref(o), ctypes.byref(s))
     out = {"status": st, "iterations": s.iterations, "gmres_total": s.gmres_total,
+           "bicgstab_total": s.bicgstab_total,
            "res_hist": list(s.res_hist[:min(s.iterations + 1, 64)]), "res_final": s.res_final}
     if raise_on_fail:
         check(st, "newton_steady")

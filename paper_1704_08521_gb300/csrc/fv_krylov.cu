@@ -479,6 +479,81 @@ static fv_status maxabs_host(const fv_grid* g, int64_t n, const double* x, doubl
   return FV_OK;
 }
 
+// BiCGstab(2) (Sleijpen & Fokkema 1993) for A_sigma x = b in the W-inner
+// product, from x (in/out), shadow residual = the initial residual; the
+// BiCGstab(l) recurrences written out for l = 2.  Section 3 runs it from the
+// last approximation of a saturated GMRES(m).  Uses Krylov columns 0..7 of
+// g->kry as r~, r_0..r_2, u_0..u_2 and scratch.  Stops when the recursive
+// residual W-norm is <= stop, after max_mv products, or on a zero BiCG / MR
+// denominator (then x is the last complete iterate).  *mv: products done.
+static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double* x, double stop,
+                           int max_mv, int prec, double sigma, double eps, int* mv,
+                           double* rnorm_out) {
+  const int64_t nv = g->nvel;
+  double* rt = g->kry;
+  double* r[3] = {g->kry + nv, g->kry + 2 * nv, g->kry + 3 * nv};
+  double* u[3] = {g->kry + 4 * nv, g->kry + 5 * nv, g->kry + 6 * nv};
+  SimpleResult sr;
+  auto apply = [&](const double* in, double* out) {
+    ++*mv;
+    return krylov_apply(g, U, in, out, nullptr, sigma, prec, eps, 200, 1.0, &sr);
+  };
+  *mv = 0;
+  FV_TRY(apply(x, r[0]));
+  FV_TRY(vec_axpby(g, nv, -1.0, r[0], 1.0, b, r[0]));
+  FV_CUDA(cudaMemcpyAsync(rt, r[0], nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  FV_CUDA(cudaMemsetAsync(u[0], 0, nv * sizeof(double), g->stream));
+  double rho0 = 1.0, alpha = 0.0, omega = 1.0, rr;
+  FV_TRY(dot_host(g, r[0], r[0], &rr));
+  double rnorm = std::sqrt(rr);
+  while (rnorm > stop && *mv + 4 <= max_mv) {
+    rho0 = -omega * rho0;
+    // BiCG part: two steps, each raising the degree of the kept powers by one
+    for (int j = 0; j < 2; ++j) {
+      double rho1, gam;
+      FV_TRY(dot_host(g, r[j], rt, &rho1));
+      if (rho0 == 0.0 || !std::isfinite(rho1)) { *rnorm_out = rnorm; return FV_OK; }
+      const double beta = alpha * rho1 / rho0;
+      rho0 = rho1;
+      for (int i = 0; i <= j; ++i) FV_TRY(vec_axpby(g, nv, 1.0, r[i], -beta, u[i], u[i]));
+      FV_TRY(apply(u[j], u[j + 1]));
+      FV_TRY(dot_host(g, u[j + 1], rt, &gam));
+      if (gam == 0.0 || !std::isfinite(gam)) { *rnorm_out = rnorm; return FV_OK; }
+      alpha = rho0 / gam;
+      for (int i = 0; i <= j; ++i) FV_TRY(vec_axpby(g, nv, 1.0, r[i], -alpha, u[i + 1], r[i]));
+      FV_TRY(apply(r[j], r[j + 1]));
+      FV_TRY(vec_axpby(g, nv, 1.0, x, alpha, u[0], x));
+    }
+    // MR part: orthogonalise r_2 against r_1, then the minimal-residual
+    // polynomial of degree 2 (gamma', gamma, gamma'' of the l = 2 case)
+    double s1, s2, c01, c12, c02;
+    FV_TRY(dot_host(g, r[1], r[1], &s1));
+    if (s1 == 0.0) { *rnorm_out = rnorm; return FV_OK; }
+    FV_TRY(dot_host(g, r[0], r[1], &c01));
+    const double gp1 = c01 / s1;
+    FV_TRY(dot_host(g, r[2], r[1], &c12));
+    const double tau12 = c12 / s1;
+    FV_TRY(vec_axpby(g, nv, 1.0, r[2], -tau12, r[1], r[2]));
+    FV_TRY(dot_host(g, r[2], r[2], &s2));
+    if (s2 == 0.0) { *rnorm_out = rnorm; return FV_OK; }
+    FV_TRY(dot_host(g, r[0], r[2], &c02));
+    const double gp2 = c02 / s2;
+    const double g2 = gp2, g1 = gp1 - tau12 * g2, gpp1 = g2;
+    omega = g2;
+    FV_TRY(vec_axpby(g, nv, 1.0, x, g1, r[0], x));
+    FV_TRY(vec_axpby(g, nv, 1.0, x, gpp1, r[1], x));
+    FV_TRY(vec_axpby(g, nv, 1.0, r[0], -gp2, r[2], r[0]));
+    FV_TRY(vec_axpby(g, nv, 1.0, r[0], -gp1, r[1], r[0]));
+    FV_TRY(vec_axpby(g, nv, 1.0, u[0], -g2, u[2], u[0]));
+    FV_TRY(vec_axpby(g, nv, 1.0, u[0], -g1, u[1], u[0]));
+    FV_TRY(dot_host(g, r[0], r[0], &rr));
+    if (!std::isfinite(rr)) { set_error("BiCGstab(2): NaN in the residual"); return FV_ENAN; }
+    rnorm = std::sqrt(rr);
+  }
+  *rnorm_out = rnorm;
+  return FV_OK;
+}
+
 }  // namespace fv
 
 using namespace fv;
@@ -606,12 +681,14 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
   if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-8;
   if (o.sigma <= 0) o.sigma = 10.0;
   if (o.simple_eps <= 0) o.simple_eps = 1e-10;
-  if (o.gmres_m > kMaxVec - 2 || (o.prec != FV_FP64 && o.prec != FV_MIXED && o.prec != FV_FF)) {
-    set_error("newton_steady: bad option (gmres_m <= 128, prec)");
+  if (o.gmres_sat <= 0) o.gmres_sat = 0.5;
+  if (o.gmres_m > kMaxVec - 2 || (o.prec != FV_FP64 && o.prec != FV_MIXED && o.prec != FV_FF) ||
+      o.linear < FV_LIN_GMRES_BICGSTAB || o.linear > FV_LIN_BICGSTAB) {
+    set_error("newton_steady: bad option (gmres_m <= 128, prec, linear)");
     return FV_EINVAL;
   }
   const int m = o.gmres_m;
-  FV_TRY(ensure_krylov(g, m + 1));
+  FV_TRY(ensure_krylov(g, std::max(m + 1, 7)));
   const int64_t nv = g->nvel;
   double* V = g->kry;
   double* Fm = g->vel_buf[1];
@@ -668,9 +745,10 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     bnorm = std::sqrt(bnorm);
     const double stop = std::max(lin_rtol * bnorm, atol);
     int its = 0;
-    bool first = true;
+    bool first = true, converged = false;
+    double prev_beta = bnorm;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol(m + 2);
-    while (true) {
+    while (o.linear != FV_LIN_BICGSTAB) {
       // r = b - A du
       if (first) {
         FV_CUDA(cudaMemcpyAsync(V, Fm, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
@@ -682,7 +760,11 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       double beta;
       FV_TRY(dot_host(g, V, V, &beta));
       beta = std::sqrt(beta);
-      if (beta <= stop || its >= o.gmres_max_it) break;
+      if (beta <= stop) { converged = true; break; }
+      if (its >= o.gmres_max_it) break;
+      // saturated: the last restart cycle cut the residual by less than gmres_sat
+      if (o.linear == FV_LIN_GMRES_BICGSTAB && its > 0 && beta > o.gmres_sat * prev_beta) break;
+      prev_beta = beta;
       FV_TRY(vec_axpby(g, nv, 1.0 / beta, V, 0.0, nullptr, V));
       std::fill(gv.begin(), gv.end(), 0.0);
       gv[0] = beta;
@@ -726,6 +808,13 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       FV_CUDA(cudaStreamSynchronize(g->stream));
     }
     st.gmres_total += its;
+    if (!converged && o.linear != FV_LIN_GMRES && its < o.gmres_max_it) {
+      int mv = 0;
+      double rn;
+      FV_TRY(bicgstab2(g, U, Fm, du, stop, o.gmres_max_it - its, cur_prec, o.sigma, o.simple_eps,
+                       &mv, &rn));
+      st.bicgstab_total += mv;
+    }
     FV_TRY(vec_axpby(g, nv, 1.0, U, -1.0, du, U));
   }
   if (stats) *stats = st;

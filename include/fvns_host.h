@@ -30,6 +30,13 @@ int fv_host_shift_steps(int m, double* H, double* Q, int nshift, const double* s
 int fv_host_ff_convert(int64_t n, const double* in, float* hi, float* lo, double* joined,
                        float* rounded);
 
+/* The float-float dot product of the mixed and float-float Krylov-basis
+ * kernels, run on the host: out = sum a_i b_i, each double split by
+ * truncation into two floats (|d - hi - lo| < 2^-46 |d|), products and sums
+ * in float-float arithmetic (about 2^-47 per step), the result joined to the
+ * nearest double.  Returns FV_EINVAL on NULL pointers or n < 0. */
+int fv_host_ff_dot(int64_t n, const double* a, const double* b, double* out);
+
 /* Float-float arithmetic check: out = (a + b) * c, operands as (hi, lo) pairs. */
 int fv_host_ff_arith(int64_t n, const float* a, const float* b, const float* c, float* out);
 

@@ -70,6 +70,7 @@ _SIGS = {
     "fv_host_shift_steps": (_I, [_I, _P, _P, _I, _P, _P]),
     "fv_host_ff_convert": (_I, [ctypes.c_int64, _P, _P, _P, _P, _P]),
     "fv_host_ff_arith": (_I, [ctypes.c_int64, _P, _P, _P, _P]),
+    "fv_host_ff_dot": (_I, [ctypes.c_int64, _P, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)

@@ -58,11 +58,15 @@ void apply_reflector(int m, double* H, double* Q, int k, int len, const double* 
 }
 
 // Francis double-shift step on the unreduced block lo..hi (hi - lo >= 2)
-// for the shift pair with sum s and product t.
-void francis_block(int m, double* H, double* Q, int lo, int hi, double s, double t) {
+// for the shift pair mid +- sqrt(disc) (disc < 0: a complex pair).  The
+// first column of (H - r1)(H - r2) is formed from the differences
+// h_ii - mid: expanding it through the sum and product of the shifts loses
+// everything when the block is close to a multiple of the identity.
+void francis_block(int m, double* H, double* Q, int lo, int hi, double mid, double disc) {
   auto a = [&](int i, int j) { return H[i * m + j]; };
-  double x = a(lo, lo) * a(lo, lo) + a(lo, lo + 1) * a(lo + 1, lo) - s * a(lo, lo) + t;
-  double y = a(lo + 1, lo) * (a(lo, lo) + a(lo + 1, lo + 1) - s);
+  const double d0 = a(lo, lo) - mid, d1 = a(lo + 1, lo + 1) - mid;
+  double x = d0 * d0 - disc + a(lo, lo + 1) * a(lo + 1, lo);
+  double y = a(lo + 1, lo) * (d0 + d1);
   double z = a(lo + 1, lo) * a(lo + 2, lo + 1);
   double v[3], beta;
   for (int k = lo; k <= hi - 2; ++k) {
@@ -126,23 +130,27 @@ bool hess_eigenvalues(int m, const double* H0, double* wr, double* wi) {
     }
     if (++total > 60 * m) return false;
     ++its;
-    double s, t;
-    if (its % 11 == 10) {          // exceptional shift
+    double mid, disc;
+    if (its % 11 == 10) {
+      // exceptional shift pair a_hh + 0.75 x +- 0.66 i x, x the size of the
+      // last two subdiagonal entries, to break a cycle of the standard shifts
       const double x = std::fabs(a(hi, hi - 1)) + std::fabs(a(hi - 1, hi - 2));
-      s = 1.5 * x;
-      t = x * x;
+      mid = a(hi, hi) + 0.75 * x;
+      disc = -0.4375 * x * x;
     } else {
-      s = a(hi - 1, hi - 1) + a(hi, hi);
-      t = a(hi - 1, hi - 1) * a(hi, hi) - a(hi - 1, hi) * a(hi, hi - 1);
+      // the eigenvalues of the trailing 2 x 2 block
+      const double hd = 0.5 * (a(hi - 1, hi - 1) - a(hi, hi));
+      mid = 0.5 * (a(hi - 1, hi - 1) + a(hi, hi));
+      disc = hd * hd + a(hi - 1, hi) * a(hi, hi - 1);
     }
-    francis_block(m, H, nullptr, lo, hi, s, t);
+    francis_block(m, H, nullptr, lo, hi, mid, disc);
   }
   return true;
 }
 
-void francis_double_step(int m, double* H, double* Q, double s, double t) {
+void francis_double_step(int m, double* H, double* Q, double re, double im) {
   if (m < 3) return;
-  francis_block(m, H, Q, 0, m - 1, s, t);
+  francis_block(m, H, Q, 0, m - 1, re, -im * im);
 }
 
 void single_shift_step(int m, double* H, double* Q, double mu) {
@@ -230,7 +238,7 @@ extern "C" int fv_host_shift_steps(int m, double* H, double* Q, int nshift, cons
   if (m < 3 || m > 512 || !H || !Q) return FV_EINVAL;
   for (int i = 0; i < nshift; ++i) {
     if (si[i] != 0.0 && i + 1 < nshift && si[i + 1] == -si[i] && sr[i + 1] == sr[i]) {
-      fv::francis_double_step(m, H, Q, 2.0 * sr[i], sr[i] * sr[i] + si[i] * si[i]);
+      fv::francis_double_step(m, H, Q, sr[i], si[i]);
       ++i;
     } else {
       fv::single_shift_step(m, H, Q, sr[i]);
@@ -251,6 +259,16 @@ extern "C" int fv_host_ff_convert(int64_t n, const double* in, float* hi, float*
     if (joined) joined[i] = fv::ff_join(s.hi, s.lo);
     if (rounded) rounded[i] = fv::f64_round_f32(in[i]);
   }
+  return FV_OK;
+}
+
+// the Krylov-basis kernels' float-float dot product on the host:
+// out = sum_i a_i b_i with the truncating split and the multiply-add
+extern "C" int fv_host_ff_dot(int64_t n, const double* a, const double* b, double* out) {
+  if (n < 0 || !a || !b || !out) return FV_EINVAL;
+  fv::ff acc{0.0f, 0.0f};
+  for (int64_t i = 0; i < n; ++i) fv::ff_mad(acc, fv::f64_split_trunc(a[i]), fv::f64_split_trunc(b[i]));
+  *out = fv::ff_join(acc.hi, acc.lo);
   return FV_OK;
 }
 

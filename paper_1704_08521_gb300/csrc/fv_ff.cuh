@@ -243,6 +243,48 @@ FF_HD ff ff_mul_f(ff x, float y) {
   return fast_two_sum(p, e);
 }
 
+// ---- Krylov-basis helpers: a truncating split and a multiply-add ---------
+//
+// f64_split_trunc(d): hi = the float of d's leading 24 significant bits,
+// lo = the float of the next 23, so |d - hi - lo| < 2^-46 |d|; integer and
+// FP32 operations only (about a dozen, no conversion instructions).
+// |d| < 2^-126 gives 0 + 0; 2^-126 <= |d| < 2^-80 gives lo = 0 (an error
+// below 2^-103; lo would not be a normal float); |d| >= 2^128, inf and nan
+// give hi = nan.
+FF_HD ff f64_split_trunc(double d) {
+  const uint64_t b = bits64(d);
+  const uint32_t h32 = (uint32_t)(b >> 32), l32 = (uint32_t)b;
+  const uint32_t sign = h32 & 0x80000000u;
+  const uint32_t e = (h32 >> 20) & 0x7ffu;
+  if (e < 897u) return {0.0f, 0.0f};
+  if (e > 1150u) return {from_bits32(0x7fc00000u), 0.0f};
+  // exponent rebiased 1023 -> 127 in place, then the top 23 fraction bits
+  const uint32_t hb = (((h32 & 0x7fffffffu) - (896u << 20)) << 3) | (l32 >> 29);
+  ff r{from_bits32(sign | hb), 0.0f};
+  const uint32_t ef = e - 896u;
+  if (ef >= 47u) {
+    // the next 23 fraction bits f: (1 + f 2^-23) 2^k - 2^k = f 2^(k-23), exact
+    // and (k >= -103) a normal float or zero
+    const uint32_t E = (ef - 23u) << 23;
+    const float t = from_bits32(E | ((l32 & 0x1fffffffu) >> 6)) - from_bits32(E);
+    r.lo = from_bits32(bits32(t) | sign);
+  }
+  return r;
+}
+
+// acc += a * b: the product by TwoProd (FMA) plus the two cross terms, added
+// by TwoSum and renormalised, so each call adds a relative error of about
+// 2^-47 of |acc| + |a b| (the lo * lo term, below 2^-46 |a b|, is dropped).
+FF_HD void ff_mad(ff& acc, ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float e = fma_f(a.hi, b.hi, -p);
+  e = fma_f(a.hi, b.lo, e);
+  e = fma_f(a.lo, b.hi, e);
+  ff s = two_sum(acc.hi, p);
+  s.lo += acc.lo + e;
+  acc = fast_two_sum(s.hi, s.lo);
+}
+
 // ---- a float-float number with arithmetic operators, so that the momentum
 // stencil template can run in ~48-bit arithmetic on the FP32 pipes
 struct ffn {

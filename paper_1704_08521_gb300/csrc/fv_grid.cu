@@ -351,6 +351,9 @@ static fv_status build(fv_grid* g) {
   FV_TRY(alloc(g, (void**)&g->d_scal, kScalars * sizeof(double)));
   g->part_len = 4096 * 130;
   FV_TRY(alloc(g, (void**)&g->d_part, g->part_len * sizeof(double)));
+  FV_TRY(alloc(g, (void**)&g->wts, g->nvel * sizeof(double)));
+  FV_TRY(alloc(g, (void**)&g->wts_ff, g->nvel * sizeof(float2)));
+  FV_TRY(fill_face_weights(g));
   FV_CUDA(cudaMallocHost((void**)&g->h_scal, kScalars * sizeof(double)));
   FV_CUDA(cudaMemset(g->d_scal, 0, kScalars * sizeof(double)));
   return FV_OK;
@@ -450,7 +453,7 @@ void fv_grid_destroy(fv_grid* g) {
                   g->vel_buf[2], g->cell_buf[0], g->cell_buf[1], g->cell_buf[2], g->tpf_buf[0],
                   g->tpf_buf[1], g->d_scal, g->d_part, g->kry, g->kry_small, g->U32, g->x32,
                   g->w32, g->vff[0], g->vff[1], g->pff, g->r32, g->phi32, g->d_met_ff,
-                  g->d_met_fn, g->Uff, g->xff, g->d_tc};
+                  g->d_met_fn, g->Uff, g->xff, g->d_tc, g->wts, g->wts_ff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_scal) cudaFreeHost(g->h_scal);

@@ -144,6 +144,8 @@ struct fv_grid {
   void* tpf_buf[2] = {nullptr, nullptr};              // n_cell doubles each (float use half)
   double* d_scal = nullptr;      // 64 device scalars
   double* d_part = nullptr;      // reduction partials
+  double* wts = nullptr;         // W: momentum control-volume size per velocity entry
+  float2* wts_ff = nullptr;      // W split into float-float pairs
   int64_t part_len = 0;
   double* h_scal = nullptr;      // pinned host mirror of d_scal
   int64_t ws_bytes = 0;
@@ -270,18 +272,22 @@ fv_status unet_guess_f32(fv_unet* u, const fv_grid* g, const float* r, float* ph
 fv_status absmax_f32_host(const fv_grid* g, const float* x, int64_t n, double* out);
 fv_status tpf_one_transform_f32(const fv_grid* g, int axis);
 
-// vector kernels (weighted inner products, Gram-Schmidt)
+// fill g->wts and g->wts_ff (the W of the inner products; 0 on wall faces)
+fv_status fill_face_weights(fv_grid* g);
+// vector kernels (weighted inner products, Gram-Schmidt); ff_arith: the
+// float-float form on the FP32 pipes (about 2^-46 relative per term) used for
+// the Krylov bases of the mixed and float-float precisions, else FP64
 fv_status vec_dots(const fv_grid* g, const double* V, int64_t ldv, int nvec, const double* w,
-                   double* d_out /* nvec, device */);
+                   double* d_out /* nvec, device */, bool ff_arith = false);
 fv_status vec_update(const fv_grid* g, double* w, const double* V, int64_t ldv, int nvec,
-                     const double* d_h, double sign);
+                     const double* d_h, double sign, bool ff_arith = false);
 fv_status vec_axpby(const fv_grid* g, int64_t n, double a, const double* x, double b,
                     const double* y, double* out);
 fv_status vec_scale_by_device(const fv_grid* g, int64_t n, const double* x, const double* d_s,
                               int mode, double* out);
 fv_status vec_combine(const fv_grid* g, const double* V, int64_t ldv, int nin,
                       const double* d_C /* nin x nout, row-major */, int nout, double* out,
-                      int64_t ldo);
+                      int64_t ldo, bool ff_arith = false);
 fv_status vec_maxabs(const fv_grid* g, int64_t n, const double* x, double* slot);
 fv_status widen_float(const fv_grid* g, const float* src, double* dst, int64_t n);
 
@@ -294,7 +300,8 @@ double bits_to_double(double slot);
 // H is m x m row-major upper Hessenberg.
 bool hess_eigenvalues(int m, const double* H, double* wr, double* wi);
 bool host_axis_tables(int n, int map, AxisBasis& B);
-void francis_double_step(int m, double* H, double* Q, double s, double t);
+// one implicit double-shift step with the shift pair re +- i im (Q accumulated)
+void francis_double_step(int m, double* H, double* Q, double re, double im);
 void single_shift_step(int m, double* H, double* Q, double mu);
 // y (complex, m) with (H - theta I) y ~ 0, unit 2-norm
 void hess_eigvec(int m, const double* H, double tr, double ti, double* yr, double* yi);

@@ -16,8 +16,8 @@ namespace fv {
 
 namespace {
 
-constexpr int kDotBlocks = 1216;     // 8 x 152 SMs
-constexpr int kDotChunk = 2048;      // elements staged per block iteration
+constexpr int kDotBlocks = 760;      // 5 x 152 SMs (40 KB of shared memory each)
+constexpr int kDotChunk = 4096;      // elements staged per block iteration (16 per thread)
 constexpr int kMaxVec = 130;
 
 // Momentum control-volume size of velocity entry e (0 on wall faces).
@@ -37,8 +37,20 @@ __device__ __forceinline__ double face_weight(const Met<double>& m, int64_t e) {
   return wx * wy * wz;
 }
 
+__global__ void k_face_weights(Met<double> m, int64_t n, double* __restrict__ W,
+                               float2* __restrict__ Wf) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = face_weight(m, e);
+    W[e] = x;
+    const ff s = f64_split_trunc(x);
+    Wf[e] = make_float2(s.hi, s.lo);
+  }
+}
+
 // partial[v][block] = sum over the block's elements of W w V_v
-__global__ void __launch_bounds__(256) k_dots(Met<double> m, const double* __restrict__ V,
+__global__ void __launch_bounds__(256, 5) k_dots(const double* __restrict__ W,
+                                              const double* __restrict__ V,
                                               int64_t ldv, int nvec,
                                               const double* __restrict__ w, int64_t n,
                                               double* __restrict__ partial) {
@@ -50,7 +62,7 @@ __global__ void __launch_bounds__(256) k_dots(Met<double> m, const double* __res
     __syncthreads();
     for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) {
       const int64_t e = e0 + t;
-      ww[t] = (e < n) ? face_weight(m, e) * w[e] : 0.0;
+      ww[t] = (e < n) ? W[e] * w[e] : 0.0;
     }
     __syncthreads();
     for (int v = 0; v < nvec; ++v) {
@@ -63,6 +75,58 @@ __global__ void __launch_bounds__(256) k_dots(Met<double> m, const double* __res
       }
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) wacc[warp][v] += s;
+    }
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += wacc[q][v];
+    partial[(int64_t)v * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// k_dots in float-float arithmetic on the FP32 pipes (the Krylov bases of
+// the mixed and float-float forms): each double is split by truncation, the
+// products and the per-thread sums are float-float, the per-warp sums are
+// added in FP64.  GB300 runs FP64 FMAs at ~1/70 of the FP32 rate, below the
+// HBM rate for one FMA per 8-byte element; this form stays HBM-bound.
+__global__ void __launch_bounds__(256, 5) k_dots_ff(const float2* __restrict__ Wf,
+                                                 const double* __restrict__ V,
+                                                 int64_t ldv, int nvec,
+                                                 const double* __restrict__ w, int64_t n,
+                                                 double* __restrict__ partial) {
+  __shared__ float2 ww[kDotChunk];
+  __shared__ double wacc[8][kMaxVec];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = threadIdx.x; v < 8 * kMaxVec; v += blockDim.x) (&wacc[0][0])[v] = 0.0;
+  for (int64_t e0 = (int64_t)blockIdx.x * kDotChunk; e0 < n; e0 += (int64_t)gridDim.x * kDotChunk) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) {
+      const int64_t e = e0 + t;
+      ff x{0.0f, 0.0f};
+      if (e < n) {
+        const float2 a = Wf[e];
+        x = ff_mul(ff{a.x, a.y}, f64_split_trunc(w[e]));
+      }
+      ww[t] = make_float2(x.hi, x.lo);
+    }
+    __syncthreads();
+    for (int v = 0; v < nvec; ++v) {
+      const double* Vv = V + (int64_t)v * ldv;
+      ff s{0.0f, 0.0f};
+#pragma unroll
+      for (int t = 0; t < kDotChunk / 256; ++t) {
+        const int64_t e = e0 + t * 256 + threadIdx.x;
+        if (e < n) {
+          const float2 a = ww[t * 256 + threadIdx.x];
+          ff_mad(s, ff{a.x, a.y}, f64_split_trunc(__ldg(Vv + e)));
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const ff q{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+        s = ff_add(s, q);
+      }
+      if (lane == 0) wacc[warp][v] += f32_to_f64(s.hi) + f32_to_f64(s.lo);
     }
   }
   __syncthreads();
@@ -98,8 +162,49 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const do
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     double s = w[e];
-    for (int v = 0; v < nvec; ++v) s += hs[v] * __ldg(V + (int64_t)v * ldv + e);
+    int v = 0;
+    for (; v + 4 <= nvec; v += 4) {
+      const double* p = V + (int64_t)v * ldv + e;
+      const double a0 = __ldg(p), a1 = __ldg(p + ldv), a2 = __ldg(p + 2 * ldv), a3 = __ldg(p + 3 * ldv);
+      s += hs[v] * a0;
+      s += hs[v + 1] * a1;
+      s += hs[v + 2] * a2;
+      s += hs[v + 3] * a3;
+    }
+    for (; v < nvec; ++v) s += hs[v] * __ldg(V + (int64_t)v * ldv + e);
     w[e] = s;
+  }
+}
+
+// k_update in float-float arithmetic (see k_dots_ff): w += sign * sum_v h[v] V_v
+__global__ void __launch_bounds__(256) k_update_ff(double* __restrict__ w,
+                                                   const double* __restrict__ V, int64_t ldv,
+                                                   int nvec, const double* __restrict__ h,
+                                                   double sign, int64_t n) {
+  __shared__ float2 hs[kMaxVec];
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+    const ff x = f64_split_trunc(sign * h[v]);
+    hs[v] = make_float2(x.hi, x.lo);
+  }
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    ff s = f64_split_trunc(w[e]);
+    int v = 0;
+    for (; v + 4 <= nvec; v += 4) {
+      const double* p = V + (int64_t)v * ldv + e;
+      const double a[4] = {__ldg(p), __ldg(p + ldv), __ldg(p + 2 * ldv), __ldg(p + 3 * ldv)};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 c = hs[v + q];
+        ff_mad(s, ff{c.x, c.y}, f64_split_trunc(a[q]));
+      }
+    }
+    for (; v < nvec; ++v) {
+      const float2 c = hs[v];
+      ff_mad(s, ff{c.x, c.y}, f64_split_trunc(__ldg(V + (int64_t)v * ldv + e)));
+    }
+    w[e] = ff_join(s.hi, s.lo);
   }
 }
 
@@ -137,6 +242,37 @@ __global__ void __launch_bounds__(256) k_combine(const double* V, int64_t ldv, i
   }
 }
 
+// k_combine in float-float arithmetic (see k_dots_ff): the nin x nout
+// coefficients are split into shared memory once per block, each block
+// stages 32 elements of every input vector as float-float pairs.
+__global__ void __launch_bounds__(256) k_combine_ff(const double* V, int64_t ldv, int nin,
+                                                    const double* __restrict__ C, int nout,
+                                                    double* out, int64_t ldo, int64_t n) {
+  extern __shared__ float2 smf[];   // nin x 32 inputs, then nin x nout coefficients
+  float2* sv = smf;
+  float2* cs = smf + nin * 32;
+  const int el = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + el;
+  for (int i = grp; i < nin; i += 8) {
+    const ff x = f64_split_trunc((e < n) ? V[(int64_t)i * ldv + e] : 0.0);
+    sv[i * 32 + el] = make_float2(x.hi, x.lo);
+  }
+  for (int q = threadIdx.x; q < nin * nout; q += blockDim.x) {
+    const ff x = f64_split_trunc(C[q]);
+    cs[q] = make_float2(x.hi, x.lo);
+  }
+  __syncthreads();
+  if (e >= n) return;
+  for (int c = grp; c < nout; c += 8) {
+    ff s{0.0f, 0.0f};
+    for (int i = 0; i < nin; ++i) {
+      const float2 a = sv[i * 32 + el], b = cs[i * nout + c];
+      ff_mad(s, ff{a.x, a.y}, ff{b.x, b.y});
+    }
+    out[(int64_t)c * ldo + e] = ff_join(s.hi, s.lo);
+  }
+}
+
 __global__ void k_maxabs(int64_t n, const double* __restrict__ x, double* slot, double* nanslot) {
   __shared__ double red[32];
   double a = 0.0;
@@ -170,15 +306,33 @@ inline unsigned grid1d(int64_t n, int per_block = 256) {
 
 }  // namespace
 
+fv_status fill_face_weights(fv_grid* g) {
+  // five 40 KB dot-product blocks per SM need the largest shared-memory split
+  FV_CUDA(cudaFuncSetAttribute(k_dots, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  FV_CUDA(cudaFuncSetAttribute(k_dots_ff, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_face_weights<<<grid1d(g->nvel), 256, 0, g->stream>>>(g->met_d, g->nvel, g->wts, g->wts_ff);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
 fv_status vec_dots(const fv_grid* g, const double* V, int64_t ldv, int nvec, const double* w,
-                   double* d_out) {
+                   double* d_out, bool ff_arith) {
   if (nvec <= 0) return FV_OK;
   if (nvec > kMaxVec) { set_error("vec_dots: too many vectors"); return FV_EINVAL; }
   const int64_t n = g->nvel;
-  const int nblk = (int)std::min<int64_t>(kDotBlocks, (n + kDotChunk - 1) / kDotChunk);
+  // chunks spread evenly: every block takes ceil(chunks / blocks) of them
+  const int64_t chunks = (n + kDotChunk - 1) / kDotChunk;
+  const int64_t per = (chunks + kDotBlocks - 1) / kDotBlocks;
+  const int nblk = (int)((chunks + per - 1) / per);
   {
     LaunchScope ls_(g, FV_K_DOTS);
-    k_dots<<<nblk, 256, 0, g->stream>>>(g->met_d, V, ldv, nvec, w, n, g->d_part);
+    if (ff_arith)
+      k_dots_ff<<<nblk, 256, 0, g->stream>>>(g->wts_ff, V, ldv, nvec, w, n, g->d_part);
+    else
+      k_dots<<<nblk, 256, 0, g->stream>>>(g->wts, V, ldv, nvec, w, n, g->d_part);
   }
   FV_CHECK_LAUNCH();
   {
@@ -190,11 +344,15 @@ fv_status vec_dots(const fv_grid* g, const double* V, int64_t ldv, int nvec, con
 }
 
 fv_status vec_update(const fv_grid* g, double* w, const double* V, int64_t ldv, int nvec,
-                     const double* d_h, double sign) {
+                     const double* d_h, double sign, bool ff_arith) {
   if (nvec <= 0) return FV_OK;
+  if (nvec > kMaxVec) { set_error("vec_update: too many vectors"); return FV_EINVAL; }
   {
     LaunchScope ls_(g, FV_K_VECTOR);
-    k_update<<<grid1d(g->nvel), 256, 0, g->stream>>>(w, V, ldv, nvec, d_h, sign, g->nvel);
+    if (ff_arith)
+      k_update_ff<<<grid1d(g->nvel), 256, 0, g->stream>>>(w, V, ldv, nvec, d_h, sign, g->nvel);
+    else
+      k_update<<<grid1d(g->nvel), 256, 0, g->stream>>>(w, V, ldv, nvec, d_h, sign, g->nvel);
   }
   FV_CHECK_LAUNCH();
   return FV_OK;
@@ -221,15 +379,22 @@ fv_status vec_scale_by_device(const fv_grid* g, int64_t n, const double* x, cons
 }
 
 fv_status vec_combine(const fv_grid* g, const double* V, int64_t ldv, int nin, const double* d_C,
-                      int nout, double* out, int64_t ldo) {
+                      int nout, double* out, int64_t ldo, bool ff_arith) {
   const int64_t n = g->nvel;
-  const size_t smem = (size_t)nin * 32 * sizeof(double);
+  const size_t smem = ff_arith ? (size_t)nin * (32 + nout) * sizeof(float2)
+                               : (size_t)nin * 32 * sizeof(double);
   if (smem > 200 * 1024) { set_error("vec_combine: too many inputs"); return FV_EINVAL; }
   if (smem > 48 * 1024)
-    FV_CUDA(cudaFuncSetAttribute(k_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FV_CUDA(cudaFuncSetAttribute(ff_arith ? (const void*)k_combine_ff : (const void*)k_combine,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     LaunchScope ls_(g, FV_K_VECTOR);
-    k_combine<<<(unsigned)((n + 31) / 32), 256, smem, g->stream>>>(V, ldv, nin, d_C, nout, out, ldo, n);
+    if (ff_arith)
+      k_combine_ff<<<(unsigned)((n + 31) / 32), 256, smem, g->stream>>>(V, ldv, nin, d_C, nout,
+                                                                       out, ldo, n);
+    else
+      k_combine<<<(unsigned)((n + 31) / 32), 256, smem, g->stream>>>(V, ldv, nin, d_C, nout, out,
+                                                                    ldo, n);
   }
   FV_CHECK_LAUNCH();
   return FV_OK;
@@ -442,15 +607,15 @@ static fv_status ensure_krylov(fv_grid* g, int cols) {
 // CGS2 of w against V[0..j] in the W-inner product; returns h (j+1) and
 // ||w||_W on the host.
 static fv_status cgs2(const fv_grid* g, const double* V, int j1, double* w, double* h_host,
-                      double* wnorm) {
+                      double* wnorm, bool ff_arith) {
   double* dh1 = g->kry_small;
   double* dh2 = g->kry_small + kMaxVec;
   double* dnn = g->kry_small + 2 * kMaxVec;
-  FV_TRY(vec_dots(g, V, g->nvel, j1, w, dh1));
-  FV_TRY(vec_update(g, w, V, g->nvel, j1, dh1, -1.0));
-  FV_TRY(vec_dots(g, V, g->nvel, j1, w, dh2));
-  FV_TRY(vec_update(g, w, V, g->nvel, j1, dh2, -1.0));
-  FV_TRY(vec_dots(g, w, g->nvel, 1, w, dnn));
+  FV_TRY(vec_dots(g, V, g->nvel, j1, w, dh1, ff_arith));
+  FV_TRY(vec_update(g, w, V, g->nvel, j1, dh1, -1.0, ff_arith));
+  FV_TRY(vec_dots(g, V, g->nvel, j1, w, dh2, ff_arith));
+  FV_TRY(vec_update(g, w, V, g->nvel, j1, dh2, -1.0, ff_arith));
+  FV_TRY(vec_dots(g, w, g->nvel, 1, w, dnn, ff_arith));
   std::vector<double> tmp(2 * kMaxVec + 1);
   FV_CUDA(cudaMemcpyAsync(tmp.data(), g->kry_small, (2 * kMaxVec + 1) * sizeof(double),
                           cudaMemcpyDeviceToHost, g->stream));
@@ -774,7 +939,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
         FV_TRY(krylov_apply(g, U, V + (int64_t)j * nv, w, nullptr, o.sigma, cur_prec, o.simple_eps,
                             200, 1.0, &sr));
         double hn;
-        FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn));
+        FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn, cur_prec != FV_FP64));
         if (hn > 0) FV_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
         for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
         H[(size_t)(j + 1) * m + j] = hn;
@@ -804,7 +969,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       }
       FV_CUDA(cudaMemcpyAsync(g->kry_small, y.data(), jdone * sizeof(double), cudaMemcpyHostToDevice,
                               g->stream));
-      FV_TRY(vec_update(g, du, V, nv, jdone, g->kry_small, 1.0));
+      FV_TRY(vec_update(g, du, V, nv, jdone, g->kry_small, 1.0, cur_prec != FV_FP64));
       FV_CUDA(cudaStreamSynchronize(g->stream));
     }
     st.gmres_total += its;
@@ -844,6 +1009,9 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
   const int64_t nv = g->nvel;
   double* V = g->kry;
   SimpleResult sr;
+  // the basis of the mixed and float-float forms is orthogonalised and
+  // recombined in float-float arithmetic (FP32 pipes), the FP64 form in FP64
+  const bool gs_ff = o.prec != FV_FP64;
   // v_0 = P x_0 / ||P x_0||
   FV_CUDA(cudaMemcpyAsync(V, v0, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
   FV_TRY(launch_zero_walls(g, V));
@@ -865,7 +1033,7 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
                           200, 1.0, &sr));
       ++matvecs;
       double hn;
-      FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn));
+      FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn, gs_ff));
       if (!(hn > 0) || !std::isfinite(hn)) { set_error("arnoldi_leading: breakdown"); return FV_ENAN; }
       FV_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
@@ -907,7 +1075,7 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
         for (int i = 0; i < m; ++i) { C[2 * i] = yr[i]; C[2 * i + 1] = yi[i]; }
         FV_CUDA(cudaMemcpyAsync(g->kry_small, C.data(), C.size() * sizeof(double),
                                 cudaMemcpyHostToDevice, g->stream));
-        FV_TRY(vec_combine(g, V, nv, m, g->kry_small, 2, evec, nv));
+        FV_TRY(vec_combine(g, V, nv, m, g->kry_small, 2, evec, nv, gs_ff));
         double a2, b2;
         FV_TRY(dot_host(g, evec, evec, &a2));
         FV_TRY(dot_host(g, evec + nv, evec + nv, &b2));
@@ -926,7 +1094,7 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
         // (a + i b)(pr + i pi) = (a pr - b pi) + i (a pi + b pr)
         const double Cph[4] = {pr * inv, pi * inv, -pi * inv, pr * inv};
         FV_CUDA(cudaMemcpyAsync(g->kry_small, Cph, 4 * sizeof(double), cudaMemcpyHostToDevice, g->stream));
-        FV_TRY(vec_combine(g, evec, nv, 2, g->kry_small, 2, evec, nv));
+        FV_TRY(vec_combine(g, evec, nv, 2, g->kry_small, 2, evec, nv, gs_ff));
         FV_CUDA(cudaStreamSynchronize(g->stream));
       }
       return FV_OK;
@@ -942,7 +1110,7 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
     for (int q = k; q < m; ++q) {
       const int id = ord[q];
       if (wi[id] != 0.0 && q + 1 < m && wi[ord[q + 1]] == -wi[id] && wr[ord[q + 1]] == wr[id]) {
-        francis_double_step(m, Hm.data(), Q.data(), 2.0 * wr[id], wr[id] * wr[id] + wi[id] * wi[id]);
+        francis_double_step(m, Hm.data(), Q.data(), wr[id], wi[id]);
         ++q;
       } else {
         single_shift_step(m, Hm.data(), Q.data(), wr[id]);
@@ -958,11 +1126,11 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
     C[(size_t)m * (k + 1) + k] = fscale;
     FV_CUDA(cudaMemcpyAsync(g->kry_small, C.data(), C.size() * sizeof(double),
                             cudaMemcpyHostToDevice, g->stream));
-    FV_TRY(vec_combine(g, V, nv, m + 1, g->kry_small, k + 1, V, nv));
+    FV_TRY(vec_combine(g, V, nv, m + 1, g->kry_small, k + 1, V, nv, gs_ff));
     // re-orthogonalise f against the kept vectors, normalise
     double* f = V + (int64_t)k * nv;
     double hn;
-    FV_TRY(cgs2(g, V, k, f, hcol.data(), &hn));
+    FV_TRY(cgs2(g, V, k, f, hcol.data(), &hn, gs_ff));
     FV_TRY(vec_axpby(g, nv, 1.0 / hn, f, 0.0, nullptr, f));
     std::fill(H.begin(), H.end(), 0.0);
     for (int i = 0; i < k; ++i)

@@ -16,8 +16,8 @@ namespace fv {
 
 namespace {
 
-constexpr int kDotBlocks = 760;      // 5 x 152 SMs (40 KB of shared memory each)
-constexpr int kDotChunk = 4096;      // elements staged per block iteration (16 per thread)
+constexpr int kDotBlocks = 304;      // 2 x 152 SMs (~104 KB of shared memory each)
+constexpr int kDotChunk = 4096;      // elements staged per block iteration
 constexpr int kMaxVec = 130;
 
 // Momentum control-volume size of velocity entry e (0 on wall faces).
@@ -48,92 +48,138 @@ __global__ void k_face_weights(Met<double> m, int64_t n, double* __restrict__ W,
   }
 }
 
-// partial[v][block] = sum over the block's elements of W w V_v
-__global__ void __launch_bounds__(256, 5) k_dots(const double* __restrict__ W,
-                                              const double* __restrict__ V,
-                                              int64_t ldv, int nvec,
-                                              const double* __restrict__ w, int64_t n,
-                                              double* __restrict__ partial) {
-  __shared__ double ww[kDotChunk];
-  __shared__ double wacc[8][kMaxVec];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = threadIdx.x; v < 8 * kMaxVec; v += blockDim.x) (&wacc[0][0])[v] = 0.0;
-  for (int64_t e0 = (int64_t)blockIdx.x * kDotChunk; e0 < n; e0 += (int64_t)gridDim.x * kDotChunk) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) {
-      const int64_t e = e0 + t;
-      ww[t] = (e < n) ? W[e] * w[e] : 0.0;
-    }
-    __syncthreads();
-    for (int v = 0; v < nvec; ++v) {
-      const double* Vv = V + (int64_t)v * ldv;
-      double s = 0.0;
-#pragma unroll
-      for (int t = 0; t < kDotChunk / 256; ++t) {
-        const int64_t e = e0 + t * 256 + threadIdx.x;
-        if (e < n) s += ww[t * 256 + threadIdx.x] * __ldg(Vv + e);
-      }
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) wacc[warp][v] += s;
-    }
-  }
-  __syncthreads();
-  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < 8; ++q) s += wacc[q][v];
-    partial[(int64_t)v * gridDim.x + blockIdx.x] = s;
-  }
-}
+// ---- weighted inner products: partial[v][block] = sum over the block's
+// elements of W w V_v.  Each block owns an even, contiguous share of the
+// elements and walks it in chunks of kDotChunk: W w is staged once per chunk
+// in shared memory, then the chunk of every V_v streams through a ring of
+// kDotStages shared-memory tiles filled by asynchronous 8-byte copies
+// (cp.async), so that the next tiles are in flight while one is reduced.
+// FF: float-float products and sums on the FP32 pipes (the bases of the
+// mixed and float-float forms; GB300's FP64 rate is below the HBM rate for
+// one multiply-add per 8-byte element); else FP64.
+constexpr int kDotTile = 2048;                        // doubles per ring tile
+constexpr int kDotStages = 4;
+constexpr int kDotTilesPerChunk = kDotChunk / kDotTile;
+constexpr size_t kDotSmem = (size_t)kDotChunk * 8 + (size_t)kDotStages * kDotTile * 8 +
+                            (size_t)8 * kMaxVec * 8;
 
-// k_dots in float-float arithmetic on the FP32 pipes (the Krylov bases of
-// the mixed and float-float forms): each double is split by truncation, the
-// products and the per-thread sums are float-float, the per-warp sums are
-// added in FP64.  GB300 runs FP64 FMAs at ~1/70 of the FP32 rate, below the
-// HBM rate for one FMA per 8-byte element; this form stays HBM-bound.
-__global__ void __launch_bounds__(256, 5) k_dots_ff(const float2* __restrict__ Wf,
-                                                 const double* __restrict__ V,
-                                                 int64_t ldv, int nvec,
-                                                 const double* __restrict__ w, int64_t n,
-                                                 double* __restrict__ partial) {
-  __shared__ float2 ww[kDotChunk];
-  __shared__ double wacc[8][kMaxVec];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = threadIdx.x; v < 8 * kMaxVec; v += blockDim.x) (&wacc[0][0])[v] = 0.0;
-  for (int64_t e0 = (int64_t)blockIdx.x * kDotChunk; e0 < n; e0 += (int64_t)gridDim.x * kDotChunk) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) {
-      const int64_t e = e0 + t;
-      ff x{0.0f, 0.0f};
-      if (e < n) {
-        const float2 a = Wf[e];
-        x = ff_mul(ff{a.x, a.y}, f64_split_trunc(w[e]));
+__device__ __forceinline__ void cpa8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// a basis entry as float-float: doubles are split, float-float pairs are taken as they are
+__device__ __forceinline__ ff to_ff(double d) { return f64_split_trunc(d); }
+__device__ __forceinline__ ff to_ff(float2 f) { return ff{f.x, f.y}; }
+__device__ __forceinline__ void put_ff(double& d, ff s) { d = ff_join(s.hi, s.lo); }
+__device__ __forceinline__ void put_ff(float2& d, ff s) { d = make_float2(s.hi, s.lo); }
+
+// VT: the basis entry type, double or (FF only) a float-float pair (hi, lo)
+template <bool FF, typename VT>
+__global__ void __launch_bounds__(256, 2) k_dots_pipe(const double* __restrict__ W,
+                                                      const float2* __restrict__ Wf,
+                                                      const VT* __restrict__ V, int64_t ldv,
+                                                      int nvec, const double* __restrict__ w,
+                                                      int64_t n, double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  double* wwd = (double*)dsm;                       // FP64: W w
+  float2* wwf = (float2*)dsm;                       // FF: W w as (hi, lo)
+  VT* ring = (VT*)(dsm + (size_t)kDotChunk * 8);
+  double* wacc = (double*)(ring + kDotStages * kDotTile);   // [8 warps][kMaxVec]
+  static_assert(sizeof(VT) == 8, "8-byte basis entries");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < 8 * kMaxVec; i += 256) wacc[i] = 0.0;
+  const int64_t lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
+  const int ntile = nvec * kDotTilesPerChunk;
+  for (int64_t e0 = lo; e0 < hi; e0 += kDotChunk) {
+    __syncthreads();                                // the previous chunk is consumed
+    auto issue = [&](int q) {                       // tile q = part q % tiles of V_{q / tiles}
+      if (q < ntile) {
+        const int v = q / kDotTilesPerChunk, part = q % kDotTilesPerChunk;
+        VT* dst = ring + (q % kDotStages) * kDotTile;
+        const int64_t b = e0 + (int64_t)part * kDotTile;
+        const VT* src = V + (int64_t)v * ldv + b;
+        for (int i = tid; i < kDotTile; i += 256)
+          if (b + i < hi) cpa8(dst + i, src + i);
       }
-      ww[t] = make_float2(x.hi, x.lo);
-    }
-    __syncthreads();
-    for (int v = 0; v < nvec; ++v) {
-      const double* Vv = V + (int64_t)v * ldv;
-      ff s{0.0f, 0.0f};
+      cpa_commit();                                 // empty groups keep the count uniform
+    };
+    for (int q = 0; q < kDotStages - 1; ++q) issue(q);
+    // W w for the chunk: the loads of 8 elements per thread in flight together
+    constexpr int kB = 8;
+    for (int t0 = 0; t0 < kDotChunk; t0 += kB * 256) {
+      double wv[kB];
+      float2 af[kB];
+      double ad[kB];
 #pragma unroll
-      for (int t = 0; t < kDotChunk / 256; ++t) {
-        const int64_t e = e0 + t * 256 + threadIdx.x;
-        if (e < n) {
-          const float2 a = ww[t * 256 + threadIdx.x];
-          ff_mad(s, ff{a.x, a.y}, f64_split_trunc(__ldg(Vv + e)));
+      for (int u = 0; u < kB; ++u) {
+        const int64_t e = e0 + t0 + u * 256 + tid;
+        const bool in = e < hi;
+        wv[u] = in ? w[e] : 0.0;
+        if constexpr (FF) af[u] = in ? Wf[e] : make_float2(0.0f, 0.0f);
+        else ad[u] = in ? W[e] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int t = t0 + u * 256 + tid;
+        if constexpr (FF) {
+          const ff x = ff_mul(ff{af[u].x, af[u].y}, f64_split_trunc(wv[u]));
+          wwf[t] = make_float2(x.hi, x.lo);
+        } else {
+          wwd[t] = ad[u] * wv[u];
         }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const ff q{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
-        s = ff_add(s, q);
+    }
+    ff sf[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};        // two chains: half the dependent latency
+    double sd = 0.0;
+    for (int q = 0; q < ntile; ++q) {
+      issue(q + kDotStages - 1);                    // into the slot consumed at q - 1
+      cpa_wait<kDotStages - 1>();                   // this thread's copies of tile q landed
+      __syncthreads();                              // everyone's copies of tile q (and W w)
+      const VT* tile = ring + (q % kDotStages) * kDotTile;
+      const int part = q % kDotTilesPerChunk;
+      const int64_t b = e0 + (int64_t)part * kDotTile;
+#pragma unroll
+      for (int t = 0; t < kDotTile / 256; ++t) {
+        const int i = t * 256 + tid;
+        if (b + i < hi) {
+          if constexpr (FF) {
+            const float2 a = wwf[part * kDotTile + i];
+            ff_mad(sf[t & 1], ff{a.x, a.y}, to_ff(tile[i]));
+          } else {
+            sd += wwd[part * kDotTile + i] * tile[i];
+          }
+        }
       }
-      if (lane == 0) wacc[warp][v] += f32_to_f64(s.hi) + f32_to_f64(s.lo);
+      if (part == kDotTilesPerChunk - 1) {          // end of V_v in this chunk: reduce
+        double r;
+        if constexpr (FF) {
+          ff t2 = ff_add(sf[0], sf[1]);
+          for (int o = 16; o > 0; o >>= 1) {
+            const ff x{__shfl_xor_sync(0xffffffffu, t2.hi, o), __shfl_xor_sync(0xffffffffu, t2.lo, o)};
+            t2 = ff_add(t2, x);
+          }
+          r = f32_to_f64(t2.hi) + f32_to_f64(t2.lo);
+          sf[0] = sf[1] = ff{0.0f, 0.0f};
+        } else {
+          for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+          r = sd;
+          sd = 0.0;
+        }
+        if (lane == 0) wacc[warp * kMaxVec + q / kDotTilesPerChunk] += r;
+      }
+      __syncthreads();                              // slot q % stages may be refilled
     }
   }
+  cpa_wait<0>();
   __syncthreads();
-  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < 8; ++q) s += wacc[q][v];
-    partial[(int64_t)v * gridDim.x + blockIdx.x] = s;
+  for (int v = tid; v < nvec; v += 256) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += wacc[q * kMaxVec + v];
+    partial[(int64_t)v * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -176,9 +222,10 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const do
   }
 }
 
-// k_update in float-float arithmetic (see k_dots_ff): w += sign * sum_v h[v] V_v
+// k_update in float-float arithmetic (see k_dots_pipe): w += sign * sum_v h[v] V_v
+template <typename VT>
 __global__ void __launch_bounds__(256) k_update_ff(double* __restrict__ w,
-                                                   const double* __restrict__ V, int64_t ldv,
+                                                   const VT* __restrict__ V, int64_t ldv,
                                                    int nvec, const double* __restrict__ h,
                                                    double sign, int64_t n) {
   __shared__ float2 hs[kMaxVec];
@@ -192,17 +239,17 @@ __global__ void __launch_bounds__(256) k_update_ff(double* __restrict__ w,
     ff s = f64_split_trunc(w[e]);
     int v = 0;
     for (; v + 4 <= nvec; v += 4) {
-      const double* p = V + (int64_t)v * ldv + e;
-      const double a[4] = {__ldg(p), __ldg(p + ldv), __ldg(p + 2 * ldv), __ldg(p + 3 * ldv)};
+      const VT* p = V + (int64_t)v * ldv + e;
+      const VT a[4] = {__ldg(p), __ldg(p + ldv), __ldg(p + 2 * ldv), __ldg(p + 3 * ldv)};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const float2 c = hs[v + q];
-        ff_mad(s, ff{c.x, c.y}, f64_split_trunc(a[q]));
+        ff_mad(s, ff{c.x, c.y}, to_ff(a[q]));
       }
     }
     for (; v < nvec; ++v) {
       const float2 c = hs[v];
-      ff_mad(s, ff{c.x, c.y}, f64_split_trunc(__ldg(V + (int64_t)v * ldv + e)));
+      ff_mad(s, ff{c.x, c.y}, to_ff(__ldg(V + (int64_t)v * ldv + e)));
     }
     w[e] = ff_join(s.hi, s.lo);
   }
@@ -242,19 +289,21 @@ __global__ void __launch_bounds__(256) k_combine(const double* V, int64_t ldv, i
   }
 }
 
-// k_combine in float-float arithmetic (see k_dots_ff): the nin x nout
+// k_combine in float-float arithmetic (see k_dots_pipe): the nin x nout
 // coefficients are split into shared memory once per block, each block
 // stages 32 elements of every input vector as float-float pairs.
-__global__ void __launch_bounds__(256) k_combine_ff(const double* V, int64_t ldv, int nin,
+template <typename VT, typename OT>
+__global__ void __launch_bounds__(256) k_combine_ff(const VT* V, int64_t ldv, int nin,
                                                     const double* __restrict__ C, int nout,
-                                                    double* out, int64_t ldo, int64_t n) {
+                                                    OT* out, int64_t ldo, int64_t n) {
   extern __shared__ float2 smf[];   // nin x 32 inputs, then nin x nout coefficients
   float2* sv = smf;
   float2* cs = smf + nin * 32;
   const int el = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int64_t e = (int64_t)blockIdx.x * 32 + el;
   for (int i = grp; i < nin; i += 8) {
-    const ff x = f64_split_trunc((e < n) ? V[(int64_t)i * ldv + e] : 0.0);
+    ff x{0.0f, 0.0f};
+    if (e < n) x = to_ff(V[(int64_t)i * ldv + e]);
     sv[i * 32 + el] = make_float2(x.hi, x.lo);
   }
   for (int q = threadIdx.x; q < nin * nout; q += blockDim.x) {
@@ -269,7 +318,25 @@ __global__ void __launch_bounds__(256) k_combine_ff(const double* V, int64_t ldv
       const float2 a = sv[i * 32 + el], b = cs[i * nout + c];
       ff_mad(s, ff{a.x, a.y}, ff{b.x, b.y});
     }
-    out[(int64_t)c * ldo + e] = ff_join(s.hi, s.lo);
+    put_ff(out[(int64_t)c * ldo + e], s);
+  }
+}
+
+// basis column <-> double vector: col = split(scale x) / x = join(col)
+__global__ void k_store_ff(int64_t n, const double* __restrict__ x, double scale,
+                           float2* __restrict__ col) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const ff s = f64_split_trunc(scale * x[e]);
+    col[e] = make_float2(s.hi, s.lo);
+  }
+}
+
+__global__ void k_load_ff(int64_t n, const float2* __restrict__ col, double* __restrict__ x) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float2 c = col[e];
+    x[e] = ff_join(c.x, c.y);
   }
 }
 
@@ -307,9 +374,13 @@ inline unsigned grid1d(int64_t n, int per_block = 256) {
 }  // namespace
 
 fv_status fill_face_weights(fv_grid* g) {
-  // five 40 KB dot-product blocks per SM need the largest shared-memory split
-  FV_CUDA(cudaFuncSetAttribute(k_dots, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  FV_CUDA(cudaFuncSetAttribute(k_dots_ff, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  // two ~104 KB dot-product blocks per SM
+  const void* dk[3] = {(const void*)k_dots_pipe<false, double>, (const void*)k_dots_pipe<true, double>,
+                       (const void*)k_dots_pipe<true, float2>};
+  for (const void* f : dk) {
+    FV_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDotSmem));
+    FV_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  }
   {
     LaunchScope ls_(g, FV_K_VECTOR);
     k_face_weights<<<grid1d(g->nvel), 256, 0, g->stream>>>(g->met_d, g->nvel, g->wts, g->wts_ff);
@@ -323,16 +394,16 @@ fv_status vec_dots(const fv_grid* g, const double* V, int64_t ldv, int nvec, con
   if (nvec <= 0) return FV_OK;
   if (nvec > kMaxVec) { set_error("vec_dots: too many vectors"); return FV_EINVAL; }
   const int64_t n = g->nvel;
-  // chunks spread evenly: every block takes ceil(chunks / blocks) of them
-  const int64_t chunks = (n + kDotChunk - 1) / kDotChunk;
-  const int64_t per = (chunks + kDotBlocks - 1) / kDotBlocks;
-  const int nblk = (int)((chunks + per - 1) / per);
+  // each block an even share of at least one chunk; two blocks per SM
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kDotBlocks, n / kDotChunk));
   {
     LaunchScope ls_(g, FV_K_DOTS);
     if (ff_arith)
-      k_dots_ff<<<nblk, 256, 0, g->stream>>>(g->wts_ff, V, ldv, nvec, w, n, g->d_part);
+      k_dots_pipe<true, double><<<nblk, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, V, ldv,
+                                                                  nvec, w, n, g->d_part);
     else
-      k_dots<<<nblk, 256, 0, g->stream>>>(g->wts, V, ldv, nvec, w, n, g->d_part);
+      k_dots_pipe<false, double><<<nblk, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, V, ldv,
+                                                                   nvec, w, n, g->d_part);
   }
   FV_CHECK_LAUNCH();
   {
@@ -350,7 +421,8 @@ fv_status vec_update(const fv_grid* g, double* w, const double* V, int64_t ldv, 
   {
     LaunchScope ls_(g, FV_K_VECTOR);
     if (ff_arith)
-      k_update_ff<<<grid1d(g->nvel), 256, 0, g->stream>>>(w, V, ldv, nvec, d_h, sign, g->nvel);
+      k_update_ff<double><<<grid1d(g->nvel), 256, 0, g->stream>>>(w, V, ldv, nvec, d_h, sign,
+                                                                  g->nvel);
     else
       k_update<<<grid1d(g->nvel), 256, 0, g->stream>>>(w, V, ldv, nvec, d_h, sign, g->nvel);
   }
@@ -385,16 +457,91 @@ fv_status vec_combine(const fv_grid* g, const double* V, int64_t ldv, int nin, c
                                : (size_t)nin * 32 * sizeof(double);
   if (smem > 200 * 1024) { set_error("vec_combine: too many inputs"); return FV_EINVAL; }
   if (smem > 48 * 1024)
-    FV_CUDA(cudaFuncSetAttribute(ff_arith ? (const void*)k_combine_ff : (const void*)k_combine,
+    FV_CUDA(cudaFuncSetAttribute(ff_arith ? (const void*)k_combine_ff<double, double>
+                                          : (const void*)k_combine,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     LaunchScope ls_(g, FV_K_VECTOR);
     if (ff_arith)
-      k_combine_ff<<<(unsigned)((n + 31) / 32), 256, smem, g->stream>>>(V, ldv, nin, d_C, nout,
-                                                                       out, ldo, n);
+      k_combine_ff<double, double><<<(unsigned)((n + 31) / 32), 256, smem, g->stream>>>(
+          V, ldv, nin, d_C, nout, out, ldo, n);
     else
       k_combine<<<(unsigned)((n + 31) / 32), 256, smem, g->stream>>>(V, ldv, nin, d_C, nout, out,
                                                                     ldo, n);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+// ---- a Krylov basis stored as float-float pairs (the mixed and float-float
+// Arnoldi bases): each vector is split once when it is stored, so the
+// Gram-Schmidt kernels read (hi, lo) pairs instead of splitting doubles
+static fv_status ffb_dots(const fv_grid* g, const float2* Vf, int nvec, const double* w,
+                          double* d_out) {
+  if (nvec <= 0) return FV_OK;
+  if (nvec > kMaxVec) { set_error("ffb_dots: too many vectors"); return FV_EINVAL; }
+  const int64_t n = g->nvel;
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kDotBlocks, n / kDotChunk));
+  {
+    LaunchScope ls_(g, FV_K_DOTS);
+    k_dots_pipe<true, float2><<<nblk, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, Vf, n, nvec,
+                                                                  w, n, g->d_part);
+  }
+  FV_CHECK_LAUNCH();
+  {
+    LaunchScope ls_(g, FV_K_DOTS);
+    k_reduce_partials<<<nvec, 256, 0, g->stream>>>(g->d_part, nblk, d_out);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+static fv_status ffb_update(const fv_grid* g, double* w, const float2* Vf, int nvec,
+                            const double* d_h, double sign) {
+  if (nvec <= 0) return FV_OK;
+  if (nvec > kMaxVec) { set_error("ffb_update: too many vectors"); return FV_EINVAL; }
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_update_ff<float2><<<grid1d(g->nvel), 256, 0, g->stream>>>(w, Vf, g->nvel, nvec, d_h, sign,
+                                                                g->nvel);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+// out_c = sum_i V_i C[i][c] (C: nin x nout on the device, row-major); out is
+// a float-float basis (may alias the first columns of Vf) or doubles
+template <typename OT>
+static fv_status ffb_combine(const fv_grid* g, const float2* Vf, int nin, const double* d_C,
+                             int nout, OT* out) {
+  const int64_t n = g->nvel;
+  const size_t smem = (size_t)nin * (32 + nout) * sizeof(float2);
+  if (smem > 200 * 1024) { set_error("ffb_combine: too many inputs"); return FV_EINVAL; }
+  if (smem > 48 * 1024)
+    FV_CUDA(cudaFuncSetAttribute(k_combine_ff<float2, OT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_combine_ff<float2, OT><<<(unsigned)((n + 31) / 32), 256, smem, g->stream>>>(
+        Vf, n, nin, d_C, nout, out, n, n);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+static fv_status ffb_store(const fv_grid* g, const double* x, double scale, float2* col) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_store_ff<<<grid1d(g->nvel), 256, 0, g->stream>>>(g->nvel, x, scale, col);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+static fv_status ffb_load(const fv_grid* g, const float2* col, double* x) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_load_ff<<<grid1d(g->nvel), 256, 0, g->stream>>>(g->nvel, col, x);
   }
   FV_CHECK_LAUNCH();
   return FV_OK;
@@ -616,6 +763,26 @@ static fv_status cgs2(const fv_grid* g, const double* V, int j1, double* w, doub
   FV_TRY(vec_dots(g, V, g->nvel, j1, w, dh2, ff_arith));
   FV_TRY(vec_update(g, w, V, g->nvel, j1, dh2, -1.0, ff_arith));
   FV_TRY(vec_dots(g, w, g->nvel, 1, w, dnn, ff_arith));
+  std::vector<double> tmp(2 * kMaxVec + 1);
+  FV_CUDA(cudaMemcpyAsync(tmp.data(), g->kry_small, (2 * kMaxVec + 1) * sizeof(double),
+                          cudaMemcpyDeviceToHost, g->stream));
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  for (int i = 0; i < j1; ++i) h_host[i] = tmp[i] + tmp[kMaxVec + i];
+  *wnorm = std::sqrt(std::max(tmp[2 * kMaxVec], 0.0));
+  return FV_OK;
+}
+
+// cgs2 against a float-float basis (w stays a double vector)
+static fv_status cgs2_ffb(const fv_grid* g, const float2* Vf, int j1, double* w, double* h_host,
+                          double* wnorm) {
+  double* dh1 = g->kry_small;
+  double* dh2 = g->kry_small + kMaxVec;
+  double* dnn = g->kry_small + 2 * kMaxVec;
+  FV_TRY(ffb_dots(g, Vf, j1, w, dh1));
+  FV_TRY(ffb_update(g, w, Vf, j1, dh1, -1.0));
+  FV_TRY(ffb_dots(g, Vf, j1, w, dh2));
+  FV_TRY(ffb_update(g, w, Vf, j1, dh2, -1.0));
+  FV_TRY(vec_dots(g, w, g->nvel, 1, w, dnn, true));
   std::vector<double> tmp(2 * kMaxVec + 1);
   FV_CUDA(cudaMemcpyAsync(tmp.data(), g->kry_small, (2 * kMaxVec + 1) * sizeof(double),
                           cudaMemcpyDeviceToHost, g->stream));
@@ -1005,21 +1172,30 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
   if (o.sigma <= 0) o.sigma = 10.0;
   if (o.simple_eps <= 0) o.simple_eps = 1e-10;
   if (o.prec != FV_FP64 && o.prec != FV_MIXED && o.prec != FV_FF) { set_error("arnoldi_leading: bad prec"); return FV_EINVAL; }
-  FV_TRY(ensure_krylov(g, m + 1));
+  // the basis of the mixed and float-float forms is stored as float-float
+  // pairs and orthogonalised and recombined in float-float arithmetic (FP32
+  // pipes): columns 0..m, then two double columns for the operand and the
+  // new vector; the FP64 form keeps an FP64 basis
+  const bool gs_ff = o.prec != FV_FP64;
+  FV_TRY(ensure_krylov(g, gs_ff ? m + 3 : m + 1));
   const int64_t nv = g->nvel;
   double* V = g->kry;
+  float2* Vf = (float2*)g->kry;
+  double* xs = g->kry + (int64_t)(m + 1) * nv;
+  double* ws = xs + nv;
   SimpleResult sr;
-  // the basis of the mixed and float-float forms is orthogonalised and
-  // recombined in float-float arithmetic (FP32 pipes), the FP64 form in FP64
-  const bool gs_ff = o.prec != FV_FP64;
   // v_0 = P x_0 / ||P x_0||
-  FV_CUDA(cudaMemcpyAsync(V, v0, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
-  FV_TRY(launch_zero_walls(g, V));
-  FV_TRY(project_inplace(g, V, nullptr, FV_MIXED, 1e-13, &sr));
+  double* x0 = gs_ff ? xs : V;
+  FV_CUDA(cudaMemcpyAsync(x0, v0, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  FV_TRY(launch_zero_walls(g, x0));
+  FV_TRY(project_inplace(g, x0, nullptr, FV_MIXED, 1e-13, &sr));
   double nrm;
-  FV_TRY(dot_host(g, V, V, &nrm));
+  FV_TRY(dot_host(g, x0, x0, &nrm));
   if (!(nrm > 0)) { set_error("arnoldi_leading: start vector has no solenoidal part"); return FV_EINVAL; }
-  FV_TRY(vec_axpby(g, nv, 1.0 / std::sqrt(nrm), V, 0.0, nullptr, V));
+  if (gs_ff)
+    FV_TRY(ffb_store(g, x0, 1.0 / std::sqrt(nrm), Vf));
+  else
+    FV_TRY(vec_axpby(g, nv, 1.0 / std::sqrt(nrm), V, 0.0, nullptr, V));
 
   std::vector<double> H((size_t)(m + 1) * m, 0.0), hcol(m + 2);
   std::vector<double> Hm((size_t)m * m), Q((size_t)m * m), wr(m), wi(m);
@@ -1028,14 +1204,25 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
   const double eps23 = std::pow(2.2204460492503131e-16, 2.0 / 3.0);
   for (int restart = 0; restart < o.max_restarts; ++restart) {
     for (int j = k; j < m; ++j) {
+      const double* xj = V + (int64_t)j * nv;
       double* w = V + (int64_t)(j + 1) * nv;
-      FV_TRY(krylov_apply(g, U, V + (int64_t)j * nv, w, nullptr, o.sigma, o.prec, o.simple_eps,
-                          200, 1.0, &sr));
+      if (gs_ff) {
+        FV_TRY(ffb_load(g, Vf + (int64_t)j * nv, xs));
+        xj = xs;
+        w = ws;
+      }
+      FV_TRY(krylov_apply(g, U, xj, w, nullptr, o.sigma, o.prec, o.simple_eps, 200, 1.0, &sr));
       ++matvecs;
       double hn;
-      FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn, gs_ff));
+      if (gs_ff)
+        FV_TRY(cgs2_ffb(g, Vf, j + 1, w, hcol.data(), &hn));
+      else
+        FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn, false));
       if (!(hn > 0) || !std::isfinite(hn)) { set_error("arnoldi_leading: breakdown"); return FV_ENAN; }
-      FV_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
+      if (gs_ff)
+        FV_TRY(ffb_store(g, w, 1.0 / hn, Vf + (int64_t)(j + 1) * nv));
+      else
+        FV_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
       H[(size_t)(j + 1) * m + j] = hn;
     }
@@ -1075,7 +1262,10 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
         for (int i = 0; i < m; ++i) { C[2 * i] = yr[i]; C[2 * i + 1] = yi[i]; }
         FV_CUDA(cudaMemcpyAsync(g->kry_small, C.data(), C.size() * sizeof(double),
                                 cudaMemcpyHostToDevice, g->stream));
-        FV_TRY(vec_combine(g, V, nv, m, g->kry_small, 2, evec, nv, gs_ff));
+        if (gs_ff)
+          FV_TRY(ffb_combine<double>(g, Vf, m, g->kry_small, 2, evec));
+        else
+          FV_TRY(vec_combine(g, V, nv, m, g->kry_small, 2, evec, nv, false));
         double a2, b2;
         FV_TRY(dot_host(g, evec, evec, &a2));
         FV_TRY(dot_host(g, evec + nv, evec + nv, &b2));
@@ -1126,12 +1316,19 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
     C[(size_t)m * (k + 1) + k] = fscale;
     FV_CUDA(cudaMemcpyAsync(g->kry_small, C.data(), C.size() * sizeof(double),
                             cudaMemcpyHostToDevice, g->stream));
-    FV_TRY(vec_combine(g, V, nv, m + 1, g->kry_small, k + 1, V, nv, gs_ff));
     // re-orthogonalise f against the kept vectors, normalise
-    double* f = V + (int64_t)k * nv;
     double hn;
-    FV_TRY(cgs2(g, V, k, f, hcol.data(), &hn, gs_ff));
-    FV_TRY(vec_axpby(g, nv, 1.0 / hn, f, 0.0, nullptr, f));
+    if (gs_ff) {
+      FV_TRY(ffb_combine<float2>(g, Vf, m + 1, g->kry_small, k + 1, Vf));
+      FV_TRY(ffb_load(g, Vf + (int64_t)k * nv, ws));
+      FV_TRY(cgs2_ffb(g, Vf, k, ws, hcol.data(), &hn));
+      FV_TRY(ffb_store(g, ws, 1.0 / hn, Vf + (int64_t)k * nv));
+    } else {
+      FV_TRY(vec_combine(g, V, nv, m + 1, g->kry_small, k + 1, V, nv, false));
+      double* f = V + (int64_t)k * nv;
+      FV_TRY(cgs2(g, V, k, f, hcol.data(), &hn, false));
+      FV_TRY(vec_axpby(g, nv, 1.0 / hn, f, 0.0, nullptr, f));
+    }
     std::fill(H.begin(), H.end(), 0.0);
     for (int i = 0; i < k; ++i)
       for (int j = 0; j < k; ++j) H[(size_t)i * m + j] = Hm[(size_t)i * m + j];

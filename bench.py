@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-eigenpair", action="store_true",
+                    help="skip the 16^3 time-to-leading-eigenpair measurement")
     return ap.parse_args()
 
 
@@ -405,11 +407,50 @@ def run_ours(args):
     mom = prof.get("momentum")
     if mom:
         res["mcell_jv_per_s"] = n ** 3 / (mom[0] / 1e3) / 1e6
+    if not args.no_eigenpair and rank == 0:
+        res["time_to_leading_eigenpair"] = eigenpair_16(fv, torch, dev, synth)
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(n, budget_s=12.0)
     if ws > 1:
         dist.destroy_process_group()
     return res
+
+
+def eigenpair_16(fv, torch, dev, synth, precs=("fp64", "mixed", "ff")):
+    """Time to the leading eigenpair on the 16^3 configuration (Re 1000, lid
+    parallel to the x sidewall, cosine grid): Newton from rest to ||F|| <
+    1e-10 by continuation in Re (200, 400, ..., 1000), then the 5 leading
+    eigenvalues by implicitly restarted Arnoldi (Krylov dimension 30, Philox
+    Gaussian start vector of seed 1, Ritz tolerance 1e-10).  Wall time around
+    the library calls, synchronised on both sides."""
+    N = 16
+    out = {"workload": "16^3 cosine grid, Re 1000, alpha 0: Newton from rest + Arnoldi(30, 5 eigenvalues)"}
+    v0 = torch.tensor(synth.gaussian_velocity((N, N, N), 1), device=dev)
+    for prec in precs:
+        g = fv.Grid(N, N, N, "cosine", alpha=0.0, re=200.0)
+        U = torch.zeros(g.n_vel, dtype=torch.float64, device=dev)
+        P = torch.zeros(g.n_cell, dtype=torch.float64, device=dev)
+        # the steady state by the FP64 form or by mixed precision (which turns
+        # to FP64 Krylov vectors near the root); Arnoldi in the form named
+        nprec = "fp64" if prec == "fp64" else "mixed"
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps = 0
+            for re in (200.0, 400.0, 600.0, 800.0, 1000.0):
+                g.set_re(re)
+                steps += fv.newton_steady(g, U, P, tol=1e-10, prec=nprec)["iterations"]
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            lam, info = fv.arnoldi_leading(g, U, v0, m=30, nev=5, prec=prec)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            out[prec] = {"newton_prec": nprec, "newton_s": t1 - t0, "arnoldi_s": t2 - t1,
+                         "total_s": t2 - t0, "newton_steps": steps,
+                         "arnoldi_matvecs": info["matvecs"], "lambda_1": [lam[0].real, lam[0].imag]}
+        except fv.FvError as e:
+            out[prec] = {"error": str(e)[:160]}
+    return out
 
 
 def oracle_solver(n):

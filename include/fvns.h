@@ -153,6 +153,9 @@ typedef struct {
  * calls never allocate.  *out receives the handle. */
 fv_status fv_grid_create(int nx, int ny, int nz, int map, double alpha, double re,
                          void* cuda_stream, fv_grid** out);
+/* Change the grid's Reynolds number (re > 0).  A change synchronises the
+ * grid's stream and drops the captured evaluation graphs, which are captured
+ * again by the next FV_MIXED / FV_FF evaluation (outside any stream capture). */
 fv_status fv_grid_set_re(fv_grid* g, double re);
 fv_status fv_grid_set_stream(fv_grid* g, void* cuda_stream);
 fv_status fv_grid_get_info(const fv_grid* g, fv_grid_info* info /* host */);
@@ -241,9 +244,10 @@ fv_status fv_critical_re(fv_grid* g, double* U, double* P, const double* v0, dou
  * mixed-precision Krylov-vector evaluation each in ONE CUDA graph launch:
  * the momentum predictors of all instances in one persistent work-queue
  * kernel, then the SIMPLE loops as concurrent graph branches, each with a
- * device-side WHILE node.  The batch borrows the grids (their workspace and
- * Re at capture time; create the batch after fv_grid_set_re).  The graph is
- * captured on the first fv_batch_krylov call (outside any stream capture). */
+ * device-side WHILE node.  The batch borrows the grids (their workspace;
+ * an instance's Re is read when fv_batch_krylov is called, so fv_grid_set_re
+ * between calls takes effect).  The graph is captured on the first
+ * fv_batch_krylov call (outside any stream capture). */
 typedef struct fv_batch fv_batch;
 fv_status fv_batch_create(int n /* 1..32 */, fv_grid* const* grids /* host array */,
                           void* cuda_stream, fv_batch** out);

@@ -563,6 +563,7 @@ struct BatchImpl {
   InstDesc* d_desc = nullptr;
   unsigned* d_counter = nullptr;
   int total_tiles = 0;
+  double re[kBatchMax] = {};      // each instance's Re when the descriptors were uploaded
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t init_node = nullptr;
@@ -579,6 +580,7 @@ static fv_status batch_descriptors(BatchImpl& b) {
     h[i].x32 = g->x32;
     h[i].w32 = g->w32;
     h[i].inv_re = float(1.0 / g->re);
+    b.re[i] = g->re;
     h[i].tile_base = base;
     base += (g->n[2] + b.ppt - 1) / b.ppt;
   }
@@ -814,6 +816,15 @@ fv_status fv_batch_krylov(fv_batch* b, const double* const* U, const double* con
   if (!B.ready || B.sigma != sigma) {
     B.sigma = sigma;
     FV_TRY(batch_build_graph(B));
+  } else {
+    // an instance's Re changed (fv_grid_set_re): the graph reads the
+    // descriptor table at run time, so uploading it again is enough
+    bool stale = false;
+    for (int i = 0; i < B.n; ++i) stale |= B.grids[i]->re != B.re[i];
+    if (stale) {
+      FV_CUDA(cudaStreamSynchronize(B.stream));
+      FV_TRY(batch_descriptors(B));
+    }
   }
   void* dcb = B.d_call;
   void* dls = B.d_loop;

@@ -402,6 +402,13 @@ fv_status fv_grid_create(int nx, int ny, int nz, int map, double alpha, double r
 
 fv_status fv_grid_set_re(fv_grid* g, double re) {
   if (!g || !(re > 0.0)) { set_error("fv_grid_set_re: bad argument"); return FV_EINVAL; }
+  if (re != g->re) {
+    // the captured evaluation graphs hold 1/Re as a kernel argument: drop
+    // them (after the work queued on the grid's stream) so that the next
+    // evaluation captures them again at the new Re
+    FV_CUDA(cudaStreamSynchronize(g->stream));
+    for (auto& c : g->graphs) destroy_graph_cache(c);
+  }
   g->re = re;
   return FV_OK;
 }

@@ -88,3 +88,31 @@ def test_batch_config4(fv, tmp_path):
     ref = layout.from_oracle(ref)
     a = O[10].cpu().numpy()
     assert np.abs(a - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+def test_batch_follows_set_re(fv):
+    """fv_grid_set_re between batch calls reaches the batched J.v: after the
+    change the batch matches single-instance evaluations at the new Re."""
+    shapes = [(12, 12, 12), (16, 12, 8)]
+    grids, U, X, O, R = [], [], [], [], []
+    for i, shape in enumerate(shapes):
+        nz, ny, nx = shape
+        g = fv.Grid(nx, ny, nz, "cosine", alpha=0.0, re=300.0)
+        grids.append(g)
+        U.append(torch.tensor(synth.vortex_base_flow(shape, "cosine", 0.0), device="cuda"))
+        X.append(torch.tensor(synth.gaussian_velocity(shape, 7 + i), device="cuda"))
+        O.append(torch.empty(g.n_vel, dtype=torch.float64, device="cuda"))
+        R.append(torch.empty(g.n_vel, dtype=torch.float64, device="cuda"))
+    b = fv.Batch(grids)
+    b.krylov(U, X, O, eps=1e-8, sigma=0.0)                # captured at Re 300
+    for g in grids:
+        g.set_re(1500.0)
+    b.krylov(U, X, O, eps=1e-8, sigma=0.0)
+    for i, shape in enumerate(shapes):
+        nz, ny, nx = shape
+        g2 = fv.Grid(nx, ny, nz, "cosine", alpha=0.0, re=1500.0)
+        fv.simple_krylov_solve(g2, U[i], X[i], R[i], None, eps=1e-8, prec="mixed")
+    torch.cuda.synchronize()
+    for o, r in zip(O, R):
+        o, r = o.cpu().numpy(), r.cpu().numpy()
+        assert np.abs(o - r).max() <= 1e-6 * np.abs(r).max()

@@ -815,9 +815,11 @@ static fv_status maxabs_host(const fv_grid* g, int64_t n, const double* x, doubl
 // product, from x (in/out), shadow residual = the initial residual; the
 // BiCGstab(l) recurrences written out for l = 2.  Section 3 runs it from the
 // last approximation of a saturated GMRES(m).  Uses Krylov columns 0..7 of
-// g->kry as r~, r_0..r_2, u_0..u_2 and scratch.  Stops when the recursive
-// residual W-norm is <= stop, after max_mv products, or on a zero BiCG / MR
-// denominator (then x is the last complete iterate).  *mv: products done.
+// g->kry as r~, r_0..r_2, u_0..u_2 and the iterate of smallest residual.
+// Stops when the recursive residual W-norm is <= stop, after max_mv
+// products, on a zero BiCG / MR denominator, or when the residual turns
+// non-finite or grows 1e6-fold over the smallest seen; x is then the
+// iterate of smallest recursive residual.  *mv: products done.
 static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double* x, double stop,
                            int max_mv, int prec, double sigma, double eps, int* mv,
                            double* rnorm_out) {
@@ -825,6 +827,7 @@ static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double*
   double* rt = g->kry;
   double* r[3] = {g->kry + nv, g->kry + 2 * nv, g->kry + 3 * nv};
   double* u[3] = {g->kry + 4 * nv, g->kry + 5 * nv, g->kry + 6 * nv};
+  double* xbest = g->kry + 7 * nv;
   SimpleResult sr;
   auto apply = [&](const double* in, double* out) {
     ++*mv;
@@ -837,20 +840,26 @@ static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double*
   FV_CUDA(cudaMemsetAsync(u[0], 0, nv * sizeof(double), g->stream));
   double rho0 = 1.0, alpha = 0.0, omega = 1.0, rr;
   FV_TRY(dot_host(g, r[0], r[0], &rr));
-  double rnorm = std::sqrt(rr);
+  double rnorm = std::sqrt(rr), best = rnorm;
+  FV_CUDA(cudaMemcpyAsync(xbest, x, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  auto finish = [&]() -> fv_status {        // hand back the best iterate
+    FV_CUDA(cudaMemcpyAsync(x, xbest, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    *rnorm_out = best;
+    return FV_OK;
+  };
   while (rnorm > stop && *mv + 4 <= max_mv) {
     rho0 = -omega * rho0;
     // BiCG part: two steps, each raising the degree of the kept powers by one
     for (int j = 0; j < 2; ++j) {
       double rho1, gam;
       FV_TRY(dot_host(g, r[j], rt, &rho1));
-      if (rho0 == 0.0 || !std::isfinite(rho1)) { *rnorm_out = rnorm; return FV_OK; }
+      if (rho0 == 0.0 || !std::isfinite(rho1)) return finish();
       const double beta = alpha * rho1 / rho0;
       rho0 = rho1;
       for (int i = 0; i <= j; ++i) FV_TRY(vec_axpby(g, nv, 1.0, r[i], -beta, u[i], u[i]));
       FV_TRY(apply(u[j], u[j + 1]));
       FV_TRY(dot_host(g, u[j + 1], rt, &gam));
-      if (gam == 0.0 || !std::isfinite(gam)) { *rnorm_out = rnorm; return FV_OK; }
+      if (gam == 0.0 || !std::isfinite(gam)) return finish();
       alpha = rho0 / gam;
       for (int i = 0; i <= j; ++i) FV_TRY(vec_axpby(g, nv, 1.0, r[i], -alpha, u[i + 1], r[i]));
       FV_TRY(apply(r[j], r[j + 1]));
@@ -860,14 +869,14 @@ static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double*
     // polynomial of degree 2 (gamma', gamma, gamma'' of the l = 2 case)
     double s1, s2, c01, c12, c02;
     FV_TRY(dot_host(g, r[1], r[1], &s1));
-    if (s1 == 0.0) { *rnorm_out = rnorm; return FV_OK; }
+    if (!(s1 > 0.0) || !std::isfinite(s1)) return finish();
     FV_TRY(dot_host(g, r[0], r[1], &c01));
     const double gp1 = c01 / s1;
     FV_TRY(dot_host(g, r[2], r[1], &c12));
     const double tau12 = c12 / s1;
     FV_TRY(vec_axpby(g, nv, 1.0, r[2], -tau12, r[1], r[2]));
     FV_TRY(dot_host(g, r[2], r[2], &s2));
-    if (s2 == 0.0) { *rnorm_out = rnorm; return FV_OK; }
+    if (!(s2 > 0.0) || !std::isfinite(s2)) return finish();
     FV_TRY(dot_host(g, r[0], r[2], &c02));
     const double gp2 = c02 / s2;
     const double g2 = gp2, g1 = gp1 - tau12 * g2, gpp1 = g2;
@@ -879,11 +888,14 @@ static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double*
     FV_TRY(vec_axpby(g, nv, 1.0, u[0], -g2, u[2], u[0]));
     FV_TRY(vec_axpby(g, nv, 1.0, u[0], -g1, u[1], u[0]));
     FV_TRY(dot_host(g, r[0], r[0], &rr));
-    if (!std::isfinite(rr)) { set_error("BiCGstab(2): NaN in the residual"); return FV_ENAN; }
     rnorm = std::sqrt(rr);
+    if (!std::isfinite(rnorm) || rnorm > 1e6 * best) return finish();
+    if (rnorm < best) {
+      best = rnorm;
+      FV_CUDA(cudaMemcpyAsync(xbest, x, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    }
   }
-  *rnorm_out = rnorm;
-  return FV_OK;
+  return finish();
 }
 
 }  // namespace fv
@@ -1020,7 +1032,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     return FV_EINVAL;
   }
   const int m = o.gmres_m;
-  FV_TRY(ensure_krylov(g, std::max(m + 1, 7)));
+  FV_TRY(ensure_krylov(g, std::max(m + 1, 8)));
   const int64_t nv = g->nvel;
   double* V = g->kry;
   double* Fm = g->vel_buf[1];
@@ -1038,20 +1050,34 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
   // linear rate of Newton near the root); the residual is always float64
   int cur_prec = o.prec;
   double prev_res = -1.0;
+  // errors inside the iteration still report the steps taken
+#define NT_TRY(x)                                   \
+  do {                                              \
+    const fv_status s_ = (x);                       \
+    if (s_ != FV_OK) {                              \
+      if (stats) *stats = st;                       \
+      return s_;                                    \
+    }                                               \
+  } while (0)
+#define NT_CUDA(x)                                                       \
+  do {                                                                   \
+    const cudaError_t e_ = (x);                                          \
+    if (e_ != cudaSuccess) NT_TRY(::fv::cuda_fail(e_, #x, __FILE__, __LINE__)); \
+  } while (0)
   for (int it = 0; it <= o.max_newton; ++it) {
     // continuity part of the Newton correction: project U
-    FV_TRY(launch_zero_walls(g, U));
-    FV_TRY(project_inplace(g, U, nullptr, FV_MIXED, 1e-13, &sr));
+    NT_TRY(launch_zero_walls(g, U));
+    NT_TRY(project_inplace(g, U, nullptr, FV_MIXED, 1e-13, &sr));
     // momentum residual with P = 0, projected: F_m = N(U) - G P(U), and
     // P(U) = (D G)^+ D N(U) accumulated by the projection
-    FV_CUDA(cudaMemsetAsync(P, 0, g->ncell * sizeof(double), g->stream));
-    FV_TRY(launch_residual(g, U, P, Fm, nullptr));
-    FV_TRY(project_inplace(g, Fm, P, FV_MIXED, 1e-13, &sr));
+    NT_CUDA(cudaMemsetAsync(P, 0, g->ncell * sizeof(double), g->stream));
+    NT_TRY(launch_residual(g, U, P, Fm, nullptr));
+    NT_TRY(project_inplace(g, Fm, P, FV_MIXED, 1e-13, &sr));
     double fmax, dmax;
     bool nan1 = false, nan2 = false;
-    FV_TRY(maxabs_host(g, nv, Fm, &fmax, &nan1));
-    FV_TRY(launch_divergence(g, U, g->cell_buf[2], nullptr));
-    FV_TRY(maxabs_host(g, g->ncell, g->cell_buf[2], &dmax, &nan2));
+    NT_TRY(maxabs_host(g, nv, Fm, &fmax, &nan1));
+    NT_TRY(launch_divergence(g, U, g->cell_buf[2], nullptr));
+    NT_TRY(maxabs_host(g, g->ncell, g->cell_buf[2], &dmax, &nan2));
     const double res = std::max(fmax, dmax);
     if (it < 64) st.res_hist[it] = res;
     st.res_final = res;
@@ -1071,9 +1097,9 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     const double lin_rtol = cur_prec == FV_MIXED ? std::max(o.gmres_rtol, 1e-6) : o.gmres_rtol;
 
     // GMRES(m) for A_sigma du = Fm, du = 0 initially
-    FV_CUDA(cudaMemsetAsync(du, 0, nv * sizeof(double), g->stream));
+    NT_CUDA(cudaMemsetAsync(du, 0, nv * sizeof(double), g->stream));
     double bnorm;
-    FV_TRY(dot_host(g, Fm, Fm, &bnorm));
+    NT_TRY(dot_host(g, Fm, Fm, &bnorm));
     bnorm = std::sqrt(bnorm);
     const double stop = std::max(lin_rtol * bnorm, atol);
     int its = 0;
@@ -1083,31 +1109,31 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     while (o.linear != FV_LIN_BICGSTAB) {
       // r = b - A du
       if (first) {
-        FV_CUDA(cudaMemcpyAsync(V, Fm, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        NT_CUDA(cudaMemcpyAsync(V, Fm, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
       } else {
-        FV_TRY(krylov_apply(g, U, du, V, nullptr, o.sigma, cur_prec, o.simple_eps, 200, 1.0, &sr));
-        FV_TRY(vec_axpby(g, nv, -1.0, V, 1.0, Fm, V));
+        NT_TRY(krylov_apply(g, U, du, V, nullptr, o.sigma, cur_prec, o.simple_eps, 200, 1.0, &sr));
+        NT_TRY(vec_axpby(g, nv, -1.0, V, 1.0, Fm, V));
       }
       first = false;
       double beta;
-      FV_TRY(dot_host(g, V, V, &beta));
+      NT_TRY(dot_host(g, V, V, &beta));
       beta = std::sqrt(beta);
       if (beta <= stop) { converged = true; break; }
       if (its >= o.gmres_max_it) break;
       // saturated: the last restart cycle cut the residual by less than gmres_sat
       if (o.linear == FV_LIN_GMRES_BICGSTAB && its > 0 && beta > o.gmres_sat * prev_beta) break;
       prev_beta = beta;
-      FV_TRY(vec_axpby(g, nv, 1.0 / beta, V, 0.0, nullptr, V));
+      NT_TRY(vec_axpby(g, nv, 1.0 / beta, V, 0.0, nullptr, V));
       std::fill(gv.begin(), gv.end(), 0.0);
       gv[0] = beta;
       int jdone = 0;
       for (int j = 0; j < m; ++j) {
         double* w = V + (int64_t)(j + 1) * nv;
-        FV_TRY(krylov_apply(g, U, V + (int64_t)j * nv, w, nullptr, o.sigma, cur_prec, o.simple_eps,
+        NT_TRY(krylov_apply(g, U, V + (int64_t)j * nv, w, nullptr, o.sigma, cur_prec, o.simple_eps,
                             200, 1.0, &sr));
         double hn;
-        FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn, cur_prec != FV_FP64));
-        if (hn > 0) FV_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
+        NT_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn, cur_prec != FV_FP64));
+        if (hn > 0) NT_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
         for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
         H[(size_t)(j + 1) * m + j] = hn;
         for (int i = 0; i < j; ++i) {
@@ -1134,21 +1160,23 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
         for (int k = i + 1; k < jdone; ++k) s -= H[(size_t)i * m + k] * y[k];
         y[i] = s / H[(size_t)i * m + i];
       }
-      FV_CUDA(cudaMemcpyAsync(g->kry_small, y.data(), jdone * sizeof(double), cudaMemcpyHostToDevice,
+      NT_CUDA(cudaMemcpyAsync(g->kry_small, y.data(), jdone * sizeof(double), cudaMemcpyHostToDevice,
                               g->stream));
-      FV_TRY(vec_update(g, du, V, nv, jdone, g->kry_small, 1.0, cur_prec != FV_FP64));
-      FV_CUDA(cudaStreamSynchronize(g->stream));
+      NT_TRY(vec_update(g, du, V, nv, jdone, g->kry_small, 1.0, cur_prec != FV_FP64));
+      NT_CUDA(cudaStreamSynchronize(g->stream));
     }
     st.gmres_total += its;
     if (!converged && o.linear != FV_LIN_GMRES && its < o.gmres_max_it) {
       int mv = 0;
       double rn;
-      FV_TRY(bicgstab2(g, U, Fm, du, stop, o.gmres_max_it - its, cur_prec, o.sigma, o.simple_eps,
+      NT_TRY(bicgstab2(g, U, Fm, du, stop, o.gmres_max_it - its, cur_prec, o.sigma, o.simple_eps,
                        &mv, &rn));
       st.bicgstab_total += mv;
     }
-    FV_TRY(vec_axpby(g, nv, 1.0, U, -1.0, du, U));
+    NT_TRY(vec_axpby(g, nv, 1.0, U, -1.0, du, U));
   }
+#undef NT_TRY
+#undef NT_CUDA
   if (stats) *stats = st;
   set_error("newton_steady: no convergence within max_newton");
   return FV_ENOCONV;

@@ -16,7 +16,7 @@ namespace fv {
 
 namespace {
 
-constexpr int kDotBlocks = 304;      // 2 x 152 SMs (~104 KB of shared memory each)
+constexpr int kDotBlocks = 456;      // 3 x 152 SMs (~40 KB of shared memory and <= 85 registers)
 constexpr int kDotChunk = 4096;      // elements staged per block iteration
 constexpr int kMaxVec = 130;
 
@@ -50,18 +50,22 @@ __global__ void k_face_weights(Met<double> m, int64_t n, double* __restrict__ W,
 
 // ---- weighted inner products: partial[v][block] = sum over the block's
 // elements of W w V_v.  Each block owns an even, contiguous share of the
-// elements and walks it in chunks of kDotChunk: W w is staged once per chunk
-// in shared memory, then the chunk of every V_v streams through a ring of
-// kDotStages shared-memory tiles filled by asynchronous 8-byte copies
-// (cp.async), so that the next tiles are in flight while one is reduced.
-// FF: float-float products and sums on the FP32 pipes (the bases of the
-// mixed and float-float forms; GB300's FP64 rate is below the HBM rate for
-// one multiply-add per 8-byte element); else FP64.
-constexpr int kDotTile = 2048;                        // doubles per ring tile
+// elements (starting at an even index) and walks it in chunks of kDotChunk,
+// 16 elements per thread: each thread keeps W w of its 16 elements in
+// registers, and the chunk of every V_v streams through a ring of kDotStages
+// shared-memory tiles of a quarter chunk, filled by asynchronous copies
+// (cp.async; 16 bytes where the basis is 16-byte aligned), so the next tiles
+// are in flight while one is reduced.  FF: float-float products and sums on
+// the FP32 pipes (the bases of the mixed and float-float forms; GB300's FP64
+// rate is below the HBM rate for one multiply-add per 8-byte element); else
+// FP64.
+constexpr int kDotPer = kDotChunk / 256;                  // elements per thread per chunk
+constexpr int kDotTile = 1024;                            // entries per ring tile
 constexpr int kDotStages = 4;
 constexpr int kDotTilesPerChunk = kDotChunk / kDotTile;
-constexpr size_t kDotSmem = (size_t)kDotChunk * 8 + (size_t)kDotStages * kDotTile * 8 +
-                            (size_t)8 * kMaxVec * 8;
+constexpr int kDotTPer = kDotTile / 256;                  // elements per thread per tile
+constexpr size_t kDotSmem = (size_t)kDotStages * kDotTile * 8 + (size_t)8 * kMaxVec * 8;
+static_assert(kDotTilesPerChunk == kDotStages, "ring slot = tile index within the chunk");
 
 __device__ __forceinline__ void cpa8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
@@ -77,101 +81,106 @@ __device__ __forceinline__ ff to_ff(float2 f) { return ff{f.x, f.y}; }
 __device__ __forceinline__ void put_ff(double& d, ff s) { d = ff_join(s.hi, s.lo); }
 __device__ __forceinline__ void put_ff(float2& d, ff s) { d = make_float2(s.hi, s.lo); }
 
-// VT: the basis entry type, double or (FF only) a float-float pair (hi, lo)
+__device__ __forceinline__ void cpa16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+
+// VT: the basis entry type, double or (FF only) a float-float pair (hi, lo);
+// al16: V and ldv allow 16-byte copies
 template <bool FF, typename VT>
-__global__ void __launch_bounds__(256, 2) k_dots_pipe(const double* __restrict__ W,
+__global__ void __launch_bounds__(256, 3) k_dots_pipe(const double* __restrict__ W,
                                                       const float2* __restrict__ Wf,
                                                       const VT* __restrict__ V, int64_t ldv,
                                                       int nvec, const double* __restrict__ w,
-                                                      int64_t n, double* __restrict__ partial) {
-  extern __shared__ __align__(16) unsigned char dsm[];
-  double* wwd = (double*)dsm;                       // FP64: W w
-  float2* wwf = (float2*)dsm;                       // FF: W w as (hi, lo)
-  VT* ring = (VT*)(dsm + (size_t)kDotChunk * 8);
-  double* wacc = (double*)(ring + kDotStages * kDotTile);   // [8 warps][kMaxVec]
+                                                      int64_t n, double* __restrict__ partial,
+                                                      int al16) {
   static_assert(sizeof(VT) == 8, "8-byte basis entries");
+  extern __shared__ __align__(16) unsigned char dsm[];
+  VT* ring = (VT*)dsm;
+  double* wacc = (double*)(dsm + (size_t)kDotStages * kDotTile * 8);   // [8 warps][kMaxVec]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 8 * kMaxVec; i += 256) wacc[i] = 0.0;
-  const int64_t lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
+  // whole chunks per block (the last block also takes the partial one)
+  const int64_t nch = (n + kDotChunk - 1) / kDotChunk;
+  const int64_t lo = (nch * blockIdx.x / gridDim.x) * kDotChunk;
+  const int64_t hi = blockIdx.x + 1 == gridDim.x ? n : (nch * (blockIdx.x + 1) / gridDim.x) * kDotChunk;
   const int ntile = nvec * kDotTilesPerChunk;
   for (int64_t e0 = lo; e0 < hi; e0 += kDotChunk) {
     __syncthreads();                                // the previous chunk is consumed
-    auto issue = [&](int q) {                       // tile q = part q % tiles of V_{q / tiles}
+    const bool full = e0 + kDotChunk <= hi;
+    const bool fast = full && al16;                 // two unguarded 16-byte copies per thread per tile
+    const VT* vchunk = V + e0 + 2 * tid;
+    auto issue = [&](int q) {                       // tile q = quarter q % 4 of V_{q / 4}
       if (q < ntile) {
         const int v = q / kDotTilesPerChunk, part = q % kDotTilesPerChunk;
-        VT* dst = ring + (q % kDotStages) * kDotTile;
-        const int64_t b = e0 + (int64_t)part * kDotTile;
-        const VT* src = V + (int64_t)v * ldv + b;
-        for (int i = tid; i < kDotTile; i += 256)
-          if (b + i < hi) cpa8(dst + i, src + i);
+        VT* dst = ring + part * kDotTile;
+        if (fast) {
+          const VT* src = vchunk + (int64_t)v * ldv + part * kDotTile;
+          cpa16(dst + 2 * tid, src);
+          cpa16(dst + 2 * tid + kDotTile / 2, src + kDotTile / 2);
+        } else {
+          const int64_t b = e0 + (int64_t)part * kDotTile;
+          const VT* src = V + (int64_t)v * ldv + b;
+          for (int i = tid; i < kDotTile; i += 256)
+            if (b + i < hi) cpa8(dst + i, src + i);
+        }
       }
       cpa_commit();                                 // empty groups keep the count uniform
     };
     for (int q = 0; q < kDotStages - 1; ++q) issue(q);
-    // W w for the chunk: the loads of 8 elements per thread in flight together
-    constexpr int kB = 8;
-    for (int t0 = 0; t0 < kDotChunk; t0 += kB * 256) {
-      double wv[kB];
-      float2 af[kB];
-      double ad[kB];
+    // W w of this thread's elements e0 + k 256 + tid, k < kDotPer
+    float2 wf[FF ? kDotPer : 1];
+    double wd[FF ? 1 : kDotPer];
 #pragma unroll
-      for (int u = 0; u < kB; ++u) {
-        const int64_t e = e0 + t0 + u * 256 + tid;
-        const bool in = e < hi;
-        wv[u] = in ? w[e] : 0.0;
-        if constexpr (FF) af[u] = in ? Wf[e] : make_float2(0.0f, 0.0f);
-        else ad[u] = in ? W[e] : 0.0;
+    for (int h = 0; h < kDotPer; h += kDotPer / 2) {    // two batches of loads in flight
+      double wv[kDotPer / 2];
+#pragma unroll
+      for (int u = 0; u < kDotPer / 2; ++u) {
+        const int k = h + u;
+        const int64_t e = e0 + k * 256 + tid;
+        wv[u] = e < hi ? w[e] : 0.0;
+        if constexpr (FF) wf[k] = e < hi ? Wf[e] : make_float2(0.0f, 0.0f);
+        else wd[k] = e < hi ? W[e] : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < kB; ++u) {
-        const int t = t0 + u * 256 + tid;
+      for (int u = 0; u < kDotPer / 2; ++u) {
+        const int k = h + u;
         if constexpr (FF) {
-          const ff x = ff_mul(ff{af[u].x, af[u].y}, f64_split_trunc(wv[u]));
-          wwf[t] = make_float2(x.hi, x.lo);
+          const ff x = ff_mul(ff{wf[k].x, wf[k].y}, f64_split_trunc(wv[u]));
+          wf[k] = make_float2(x.hi, x.lo);
         } else {
-          wwd[t] = ad[u] * wv[u];
+          wd[k] *= wv[u];
         }
       }
     }
-    ff sf[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};        // two chains: half the dependent latency
-    double sd = 0.0;
-    for (int q = 0; q < ntile; ++q) {
-      issue(q + kDotStages - 1);                    // into the slot consumed at q - 1
-      cpa_wait<kDotStages - 1>();                   // this thread's copies of tile q landed
-      __syncthreads();                              // everyone's copies of tile q (and W w)
-      const VT* tile = ring + (q % kDotStages) * kDotTile;
-      const int part = q % kDotTilesPerChunk;
-      const int64_t b = e0 + (int64_t)part * kDotTile;
+    for (int v = 0; v < nvec; ++v) {
+      ff sf{0.0f, 0.0f};
+      double sd = 0.0;
 #pragma unroll
-      for (int t = 0; t < kDotTile / 256; ++t) {
-        const int i = t * 256 + tid;
-        if (b + i < hi) {
-          if constexpr (FF) {
-            const float2 a = wwf[part * kDotTile + i];
-            ff_mad(sf[t & 1], ff{a.x, a.y}, to_ff(tile[i]));
-          } else {
-            sd += wwd[part * kDotTile + i] * tile[i];
+      for (int part = 0; part < kDotTilesPerChunk; ++part) {
+        issue(v * kDotTilesPerChunk + part + kDotStages - 1);   // into the slot freed at q - 1
+        cpa_wait<kDotStages - 1>();                 // this thread's copies of tile q landed
+        __syncthreads();                            // everyone's copies of tile q
+        const VT* tile = ring + part * kDotTile;
+#pragma unroll
+        for (int t = 0; t < kDotTPer; ++t) {
+          const int i = t * 256 + tid;
+          const int k = part * kDotTPer + t;
+          if (full || e0 + part * kDotTile + i < hi) {
+            if constexpr (FF) ff_mad(sf, ff{wf[k].x, wf[k].y}, to_ff(tile[i]));
+            else sd += wd[k] * tile[i];
           }
         }
+        __syncthreads();                            // the slot may be refilled
       }
-      if (part == kDotTilesPerChunk - 1) {          // end of V_v in this chunk: reduce
-        double r;
-        if constexpr (FF) {
-          ff t2 = ff_add(sf[0], sf[1]);
-          for (int o = 16; o > 0; o >>= 1) {
-            const ff x{__shfl_xor_sync(0xffffffffu, t2.hi, o), __shfl_xor_sync(0xffffffffu, t2.lo, o)};
-            t2 = ff_add(t2, x);
-          }
-          r = f32_to_f64(t2.hi) + f32_to_f64(t2.lo);
-          sf[0] = sf[1] = ff{0.0f, 0.0f};
-        } else {
-          for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
-          r = sd;
-          sd = 0.0;
-        }
-        if (lane == 0) wacc[warp * kMaxVec + q / kDotTilesPerChunk] += r;
-      }
-      __syncthreads();                              // slot q % stages may be refilled
+      // per thread the partial sum of 16 products; across the warp in FP64
+      // (a double holds the float-float value; a few FP64 adds per 16 elements)
+      double r;
+      if constexpr (FF) r = (double)sf.hi + (double)sf.lo;
+      else r = sd;
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+      if (lane == 0) wacc[warp * kMaxVec + v] += r;
     }
   }
   cpa_wait<0>();
@@ -374,7 +383,7 @@ inline unsigned grid1d(int64_t n, int per_block = 256) {
 }  // namespace
 
 fv_status fill_face_weights(fv_grid* g) {
-  // two ~104 KB dot-product blocks per SM
+  // three ~40 KB dot-product blocks per SM
   const void* dk[3] = {(const void*)k_dots_pipe<false, double>, (const void*)k_dots_pipe<true, double>,
                        (const void*)k_dots_pipe<true, float2>};
   for (const void* f : dk) {
@@ -395,15 +404,16 @@ fv_status vec_dots(const fv_grid* g, const double* V, int64_t ldv, int nvec, con
   if (nvec > kMaxVec) { set_error("vec_dots: too many vectors"); return FV_EINVAL; }
   const int64_t n = g->nvel;
   // each block an even share of at least one chunk; two blocks per SM
-  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kDotBlocks, n / kDotChunk));
+  const int nblk = (int)std::min<int64_t>(kDotBlocks, (n + kDotChunk - 1) / kDotChunk);
   {
     LaunchScope ls_(g, FV_K_DOTS);
+    const int al16 = ((uintptr_t)V % 16 == 0) && (ldv % 2 == 0);
     if (ff_arith)
       k_dots_pipe<true, double><<<nblk, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, V, ldv,
-                                                                  nvec, w, n, g->d_part);
+                                                                  nvec, w, n, g->d_part, al16);
     else
       k_dots_pipe<false, double><<<nblk, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, V, ldv,
-                                                                   nvec, w, n, g->d_part);
+                                                                   nvec, w, n, g->d_part, al16);
   }
   FV_CHECK_LAUNCH();
   {
@@ -481,11 +491,12 @@ static fv_status ffb_dots(const fv_grid* g, const float2* Vf, int nvec, const do
   if (nvec <= 0) return FV_OK;
   if (nvec > kMaxVec) { set_error("ffb_dots: too many vectors"); return FV_EINVAL; }
   const int64_t n = g->nvel;
-  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kDotBlocks, n / kDotChunk));
+  const int nblk = (int)std::min<int64_t>(kDotBlocks, (n + kDotChunk - 1) / kDotChunk);
   {
     LaunchScope ls_(g, FV_K_DOTS);
+    const int al16 = ((uintptr_t)Vf % 16 == 0) && (n % 2 == 0);
     k_dots_pipe<true, float2><<<nblk, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, Vf, n, nvec,
-                                                                  w, n, g->d_part);
+                                                                  w, n, g->d_part, al16);
   }
   FV_CHECK_LAUNCH();
   {

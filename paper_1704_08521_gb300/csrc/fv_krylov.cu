@@ -174,13 +174,24 @@ __global__ void __launch_bounds__(256, 3) k_dots_pipe(const double* __restrict__
         }
         __syncthreads();                            // the slot may be refilled
       }
-      // per thread the partial sum of 16 products; across the warp in FP64
-      // (a double holds the float-float value; a few FP64 adds per 16 elements)
-      double r;
-      if constexpr (FF) r = (double)sf.hi + (double)sf.lo;
-      else r = sd;
-      for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-      if (lane == 0) wacc[warp * kMaxVec + v] += r;
+      // per thread the partial sum of 16 products, then across the warp: in
+      // float-float on the FP32 pipes (one TwoSum per level; FP64 adds and
+      // conversions here would load GB300's slow FP64 pipe once per 2 elements)
+      if constexpr (FF) {
+        ff t = sf;
+        for (int o = 16; o > 0; o >>= 1) {
+          const float xh = __shfl_xor_sync(0xffffffffu, t.hi, o);
+          const float xl = __shfl_xor_sync(0xffffffffu, t.lo, o);
+          ff u = two_sum(t.hi, xh);
+          u.lo += t.lo + xl;
+          t = fast_two_sum(u.hi, u.lo);
+        }
+        if (lane == 0) wacc[warp * kMaxVec + v] += (double)t.hi + (double)t.lo;
+      } else {
+        double r = sd;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if (lane == 0) wacc[warp * kMaxVec + v] += r;
+      }
     }
   }
   cpa_wait<0>();
@@ -259,6 +270,58 @@ __global__ void __launch_bounds__(256) k_update_ff(double* __restrict__ w,
     for (; v < nvec; ++v) {
       const float2 c = hs[v];
       ff_mad(s, ff{c.x, c.y}, to_ff(__ldg(V + (int64_t)v * ldv + e)));
+    }
+    w[e] = ff_join(s.hi, s.lo);
+  }
+}
+
+// k_update_ff for a float-float basis, two adjacent elements per thread with
+// 16-byte loads (w, V and ldv 16-byte aligned / even); the odd last element,
+// if any, by the first thread
+__global__ void __launch_bounds__(256) k_update_ffb2(double* __restrict__ w,
+                                                     const float2* __restrict__ V, int64_t ldv,
+                                                     int nvec, const double* __restrict__ h,
+                                                     double sign, int64_t n) {
+  __shared__ float2 hs[kMaxVec];
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+    const ff x = f64_split_trunc(sign * h[v]);
+    hs[v] = make_float2(x.hi, x.lo);
+  }
+  __syncthreads();
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t np = n / 2;
+  for (int64_t pi = gt; pi < np; pi += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = 2 * pi;
+    const double2 wv = *reinterpret_cast<const double2*>(w + e);
+    ff s0 = f64_split_trunc(wv.x), s1 = f64_split_trunc(wv.y);
+    int v = 0;
+    for (; v + 4 <= nvec; v += 4) {
+      const float2* p = V + (int64_t)v * ldv + e;
+      const float4 a[4] = {__ldg(reinterpret_cast<const float4*>(p)),
+                           __ldg(reinterpret_cast<const float4*>(p + ldv)),
+                           __ldg(reinterpret_cast<const float4*>(p + 2 * ldv)),
+                           __ldg(reinterpret_cast<const float4*>(p + 3 * ldv))};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 c = hs[v + q];
+        ff_mad(s0, ff{c.x, c.y}, ff{a[q].x, a[q].y});
+        ff_mad(s1, ff{c.x, c.y}, ff{a[q].z, a[q].w});
+      }
+    }
+    for (; v < nvec; ++v) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(V + (int64_t)v * ldv + e));
+      const float2 c = hs[v];
+      ff_mad(s0, ff{c.x, c.y}, ff{a.x, a.y});
+      ff_mad(s1, ff{c.x, c.y}, ff{a.z, a.w});
+    }
+    *reinterpret_cast<double2*>(w + e) = make_double2(ff_join(s0.hi, s0.lo), ff_join(s1.hi, s1.lo));
+  }
+  if (gt == 0 && (n & 1)) {
+    const int64_t e = n - 1;
+    ff s = f64_split_trunc(w[e]);
+    for (int v = 0; v < nvec; ++v) {
+      const float2 c = hs[v];
+      ff_mad(s, ff{c.x, c.y}, to_ff(V[(int64_t)v * ldv + e]));
     }
     w[e] = ff_join(s.hi, s.lo);
   }
@@ -513,8 +576,11 @@ static fv_status ffb_update(const fv_grid* g, double* w, const float2* Vf, int n
   if (nvec > kMaxVec) { set_error("ffb_update: too many vectors"); return FV_EINVAL; }
   {
     LaunchScope ls_(g, FV_K_VECTOR);
-    k_update_ff<float2><<<grid1d(g->nvel), 256, 0, g->stream>>>(w, Vf, g->nvel, nvec, d_h, sign,
-                                                                g->nvel);
+    const int64_t n = g->nvel;
+    if ((uintptr_t)w % 16 == 0 && (uintptr_t)Vf % 16 == 0 && n % 2 == 0)
+      k_update_ffb2<<<grid1d(n / 2 + 1), 256, 0, g->stream>>>(w, Vf, n, nvec, d_h, sign, n);
+    else
+      k_update_ff<float2><<<grid1d(n), 256, 0, g->stream>>>(w, Vf, n, nvec, d_h, sign, n);
   }
   FV_CHECK_LAUNCH();
   return FV_OK;

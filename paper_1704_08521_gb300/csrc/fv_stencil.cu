@@ -33,9 +33,11 @@ __global__ void __launch_bounds__(256) k_momentum(Met<T> m, const TI* __restrict
   const int i = act_ ? t_ % m.n[0] : 0;
   const int j = act_ ? t_ / m.n[0] : 0;
   if (!act_) return;
+  // the planes unrolled so that their loads are in flight together
+#pragma unroll
   for (int kk = 0; kk < kCellKz; ++kk) {
   const int k = blockIdx.y * kCellKz + kk;
-  if (k >= m.n[2]) return;
+  if (k >= m.n[2]) continue;
   const int pos[3] = {i, j, k};
   const int st[3] = {1, m.n[0], m.n[0] * m.n[1]};
   const int base = (k * m.n[1] + j) * m.n[0] + i;

@@ -192,9 +192,10 @@ __global__ void __launch_bounds__(1024) k_decide(const float* __restrict__ part,
 }
 
 __global__ void k_join_g(const float2* __restrict__ vff0, const float2* __restrict__ vff1,
-                         const float2* __restrict__ pff, const LoopState* __restrict__ ls,
+                         const float2* __restrict__ pff, LoopState* __restrict__ ls,
                          const CallBlock* __restrict__ cb, int64_t nvel, int64_t ncell) {
   const float2* v = ((ls->pass - 1) & 1) ? vff1 : vff0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && ls->status > ls->worst) ls->worst = ls->status;
   const double* x = cb->x;
   double* out = cb->out;
   double* p = cb->p;
@@ -226,6 +227,7 @@ inline int block_x(const fv_grid*) { return kCellThreads; }
 static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc, int prec = FV_MIXED) {
   FV_CUDA(cudaMalloc(&gc.d_call, sizeof(CallBlock)));
   FV_CUDA(cudaMalloc((void**)&gc.d_loop, sizeof(LoopState)));
+  FV_CUDA(cudaMemset(gc.d_loop, 0, sizeof(LoopState)));
   cudaStream_t cs;
   FV_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   const cudaStream_t saved = g->stream;
@@ -395,6 +397,19 @@ fv_status mixed_krylov_graph(const fv_grid* gcst, const double* U, const double*
   if (phil) *phil = hls.phi_last;
   if (divl) *divl = hls.div_last;
   if (status) *status = hls.status;
+  return FV_OK;
+}
+
+fv_status graph_take_status(fv_grid* g, int* worst) {
+  *worst = 0;
+  for (auto& c : g->graphs) {
+    if (!c.ready) continue;
+    int w = 0;
+    FV_CUDA(cudaMemcpyAsync(&w, &c.d_loop->worst, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    FV_CUDA(cudaMemsetAsync(&c.d_loop->worst, 0, sizeof(int), g->stream));
+    FV_CUDA(cudaStreamSynchronize(g->stream));
+    *worst = std::max(*worst, w);
+  }
   return FV_OK;
 }
 

@@ -98,7 +98,10 @@ struct TcMats {
 // device-side state of one SIMPLE loop (graph path)
 struct LoopState {
   float phi1, phi_prev, phi_last, div_last;
-  int pass, nan, status, pad;   // status: 0 running, 1 converged, 2 pass cap, 3 NaN
+  int pass, nan, status;        // status: 0 running, 1 converged, 2 pass cap, 3 NaN
+  int worst;                    // largest status of the evaluations since graph_take_status
+                                // (kept across evaluations: lets drivers launch them
+                                // asynchronously and check once per cycle)
 };
 
 // one captured, instantiated evaluation graph (per grid and shift sigma)
@@ -272,6 +275,9 @@ fv_status unet_guess_f32(fv_unet* u, const fv_grid* g, const float* r, float* ph
 fv_status absmax_f32_host(const fv_grid* g, const float* x, int64_t n, double* out);
 fv_status tpf_one_transform_f32(const fv_grid* g, int axis);
 
+// the largest status (1 converged, 2 pass cap, 3 NaN; 0 none) of the graph
+// evaluations on g since the last call, then reset (synchronises g's stream)
+fv_status graph_take_status(fv_grid* g, int* worst);
 // fill g->wts and g->wts_ff (the W of the inner products; 0 on wall faces)
 fv_status fill_face_weights(fv_grid* g);
 // vector kernels (weighted inner products, Gram-Schmidt); ff_arith: the

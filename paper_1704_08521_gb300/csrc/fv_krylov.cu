@@ -668,8 +668,10 @@ struct SimpleResult {
 };
 
 static fv_status simple_loop(const fv_grid* g, double* cur, double* spare, double* out, double* p,
-                             double eps, int max_pass, int prec, double omega, SimpleResult* res,
+                             double eps, int max_pass, int prec, double omega, SimpleResult* res_out,
                              double div_abs = 0.0) {
+  SimpleResult local;
+  SimpleResult* res = res_out ? res_out : &local;
   double* r = g->cell_buf[0];
   void* phi = (void*)g->cell_buf[1];
   FV_TRY(reset_scalars(g));
@@ -801,6 +803,20 @@ static fv_status krylov_apply(const fv_grid* g, const double* U, const double* x
 
 static fv_status maxabs_host(const fv_grid* g, int64_t n, const double* x, double* out, bool* nan);
 
+// The Krylov drivers launch graph evaluations without waiting for their
+// status (krylov_apply with res = nullptr) and check, once per cycle, the
+// worst status since the last check: the error krylov_apply would have
+// returned for any of them.  Host-driven evaluations report at once.
+static fv_status check_products(const fv_grid* gc, int prec) {
+  fv_grid* g = const_cast<fv_grid*>(gc);
+  if (!(g->use_graph && (prec == FV_MIXED || prec == FV_FF))) return FV_OK;
+  int w = 0;
+  FV_TRY(graph_take_status(g, &w));
+  if (w == 3) { set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN; }
+  if (w == 2) { set_error("SIMPLE loop reached max_pass"); return FV_ENOCONV; }
+  return FV_OK;
+}
+
 // Project x in place onto divergence-free fields (p: optional pressure out),
 // until the divergence is at round-off level for the size of x.
 static fv_status project_inplace(const fv_grid* g, double* x, double* p, int prec, double eps,
@@ -878,6 +894,17 @@ static fv_status dot_host(const fv_grid* g, const double* a, const double* b, do
   return FV_OK;
 }
 
+// W-inner products of nvec columns of V (stride ldv) with w, to the host in
+// one synchronisation (FP64)
+static fv_status dots_host(const fv_grid* g, const double* V, int64_t ldv, int nvec,
+                           const double* w, double* out) {
+  double* d = g->kry_small + 3 * kMaxVec;
+  FV_TRY(vec_dots(g, V, ldv, nvec, w, d));
+  FV_CUDA(cudaMemcpyAsync(out, d, nvec * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  return FV_OK;
+}
+
 static fv_status maxabs_host(const fv_grid* g, int64_t n, const double* x, double* out, bool* nan) {
   FV_TRY(reset_scalars(g));
   FV_TRY(vec_maxabs(g, n, x, g->d_scal + S_RED + 1));
@@ -905,21 +932,25 @@ static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double*
   double* r[3] = {g->kry + nv, g->kry + 2 * nv, g->kry + 3 * nv};
   double* u[3] = {g->kry + 4 * nv, g->kry + 5 * nv, g->kry + 6 * nv};
   double* xbest = g->kry + 7 * nv;
-  SimpleResult sr;
   auto apply = [&](const double* in, double* out) {
     ++*mv;
-    return krylov_apply(g, U, in, out, nullptr, sigma, prec, eps, 200, 1.0, &sr);
+    return krylov_apply(g, U, in, out, nullptr, sigma, prec, eps, 200, 1.0, nullptr);
   };
   *mv = 0;
   FV_TRY(apply(x, r[0]));
   FV_TRY(vec_axpby(g, nv, -1.0, r[0], 1.0, b, r[0]));
   FV_CUDA(cudaMemcpyAsync(rt, r[0], nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
   FV_CUDA(cudaMemsetAsync(u[0], 0, nv * sizeof(double), g->stream));
-  double rho0 = 1.0, alpha = 0.0, omega = 1.0, rr;
-  FV_TRY(dot_host(g, r[0], r[0], &rr));
+  double rho0 = 1.0, alpha = 0.0, omega = 1.0, rr, rho_next;
+  // (r~, r_0) and (r_0, r_0) in one pass: r~ and r_0 are adjacent columns
+  double d2[3];
+  FV_TRY(dots_host(g, rt, nv, 2, r[0], d2));
+  rho_next = d2[0];
+  rr = d2[1];
   double rnorm = std::sqrt(rr), best = rnorm;
   FV_CUDA(cudaMemcpyAsync(xbest, x, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
   auto finish = [&]() -> fv_status {        // hand back the best iterate
+    FV_TRY(check_products(g, prec));
     FV_CUDA(cudaMemcpyAsync(x, xbest, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
     *rnorm_out = best;
     return FV_OK;
@@ -929,7 +960,8 @@ static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double*
     // BiCG part: two steps, each raising the degree of the kept powers by one
     for (int j = 0; j < 2; ++j) {
       double rho1, gam;
-      FV_TRY(dot_host(g, r[j], rt, &rho1));
+      if (j == 0) rho1 = rho_next;                 // from the end of the previous cycle
+      else FV_TRY(dot_host(g, r[j], rt, &rho1));
       if (rho0 == 0.0 || !std::isfinite(rho1)) return finish();
       const double beta = alpha * rho1 / rho0;
       rho0 = rho1;
@@ -944,17 +976,18 @@ static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double*
     }
     // MR part: orthogonalise r_2 against r_1, then the minimal-residual
     // polynomial of degree 2 (gamma', gamma, gamma'' of the l = 2 case)
-    double s1, s2, c01, c12, c02;
-    FV_TRY(dot_host(g, r[1], r[1], &s1));
+    // (r_0, r_1), (r_1, r_1), (r_2, r_1) in one pass (r_0..r_2 are adjacent
+    // columns), then (r_0, r_2), (r_2, r_2) after r_2 is orthogonalised
+    double d3[3];
+    FV_TRY(dots_host(g, r[0], nv, 3, r[1], d3));
+    const double c01 = d3[0], s1 = d3[1], c12 = d3[2];
     if (!(s1 > 0.0) || !std::isfinite(s1)) return finish();
-    FV_TRY(dot_host(g, r[0], r[1], &c01));
     const double gp1 = c01 / s1;
-    FV_TRY(dot_host(g, r[2], r[1], &c12));
     const double tau12 = c12 / s1;
     FV_TRY(vec_axpby(g, nv, 1.0, r[2], -tau12, r[1], r[2]));
-    FV_TRY(dot_host(g, r[2], r[2], &s2));
+    FV_TRY(dots_host(g, r[0], 2 * nv, 2, r[2], d2));
+    const double c02 = d2[0], s2 = d2[1];
     if (!(s2 > 0.0) || !std::isfinite(s2)) return finish();
-    FV_TRY(dot_host(g, r[0], r[2], &c02));
     const double gp2 = c02 / s2;
     const double g2 = gp2, g1 = gp1 - tau12 * g2, gpp1 = g2;
     omega = g2;
@@ -964,7 +997,10 @@ static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double*
     FV_TRY(vec_axpby(g, nv, 1.0, r[0], -gp1, r[1], r[0]));
     FV_TRY(vec_axpby(g, nv, 1.0, u[0], -g2, u[2], u[0]));
     FV_TRY(vec_axpby(g, nv, 1.0, u[0], -g1, u[1], u[0]));
-    FV_TRY(dot_host(g, r[0], r[0], &rr));
+    FV_TRY(dots_host(g, rt, nv, 2, r[0], d2));
+    FV_TRY(check_products(g, prec));
+    rho_next = d2[0];
+    rr = d2[1];
     rnorm = std::sqrt(rr);
     if (!std::isfinite(rnorm) || rnorm > 1e6 * best) return finish();
     if (rnorm < best) {
@@ -1110,6 +1146,10 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
   }
   const int m = o.gmres_m;
   FV_TRY(ensure_krylov(g, std::max(m + 1, 8)));
+  {
+    int w;                                     // forget statuses of earlier evaluations
+    FV_TRY(graph_take_status(g, &w));
+  }
   const int64_t nv = g->nvel;
   double* V = g->kry;
   double* Fm = g->vel_buf[1];
@@ -1188,7 +1228,8 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       if (first) {
         NT_CUDA(cudaMemcpyAsync(V, Fm, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
       } else {
-        NT_TRY(krylov_apply(g, U, du, V, nullptr, o.sigma, cur_prec, o.simple_eps, 200, 1.0, &sr));
+        NT_TRY(krylov_apply(g, U, du, V, nullptr, o.sigma, cur_prec, o.simple_eps, 200, 1.0,
+                            nullptr));
         NT_TRY(vec_axpby(g, nv, -1.0, V, 1.0, Fm, V));
       }
       first = false;
@@ -1207,7 +1248,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       for (int j = 0; j < m; ++j) {
         double* w = V + (int64_t)(j + 1) * nv;
         NT_TRY(krylov_apply(g, U, V + (int64_t)j * nv, w, nullptr, o.sigma, cur_prec, o.simple_eps,
-                            200, 1.0, &sr));
+                            200, 1.0, nullptr));
         double hn;
         NT_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn, cur_prec != FV_FP64));
         if (hn > 0) NT_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
@@ -1230,6 +1271,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
         jdone = j + 1;
         if (std::fabs(gv[j + 1]) <= stop || its >= o.gmres_max_it || hn == 0) break;
       }
+      NT_TRY(check_products(g, cur_prec));
       // y = R^{-1} g ; du += V y
       std::vector<double> y(jdone);
       for (int i = jdone - 1; i >= 0; --i) {
@@ -1283,6 +1325,10 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
   // new vector; the FP64 form keeps an FP64 basis
   const bool gs_ff = o.prec != FV_FP64;
   FV_TRY(ensure_krylov(g, gs_ff ? m + 3 : m + 1));
+  {
+    int w;                                     // forget statuses of earlier evaluations
+    FV_TRY(graph_take_status(g, &w));
+  }
   const int64_t nv = g->nvel;
   double* V = g->kry;
   float2* Vf = (float2*)g->kry;
@@ -1316,7 +1362,7 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
         xj = xs;
         w = ws;
       }
-      FV_TRY(krylov_apply(g, U, xj, w, nullptr, o.sigma, o.prec, o.simple_eps, 200, 1.0, &sr));
+      FV_TRY(krylov_apply(g, U, xj, w, nullptr, o.sigma, o.prec, o.simple_eps, 200, 1.0, nullptr));
       ++matvecs;
       double hn;
       if (gs_ff)
@@ -1331,6 +1377,7 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
       H[(size_t)(j + 1) * m + j] = hn;
     }
+    FV_TRY(check_products(g, o.prec));
     for (int i = 0; i < m; ++i)
       for (int j = 0; j < m; ++j) Hm[(size_t)i * m + j] = H[(size_t)i * m + j];
     if (!hess_eigenvalues(m, Hm.data(), wr.data(), wi.data())) {

@@ -276,3 +276,24 @@ def test_ff_newton_continuation_is_quadratic(fv):
         g.set_re(re)
         st = fv.newton_steady(g, U, P, tol=1e-10, prec="ff", max_newton=8)
         assert st["res_final"] < 1e-10, (re, st["res_hist"])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "ff"])
+def test_nan_in_operator_is_reported(fv, prec):
+    """Krylov drivers launch the evaluation graphs without reading their status
+    back; a NaN in the base flow must still end Arnoldi and Newton with an
+    error (the graph's sticky status, or the NaN reaching a dot product)."""
+    n = 8
+    g = fv.Grid(n, n, n, "cosine", alpha=0.0, re=300.0)
+    U = dev(synth.vortex_base_flow((n, n, n), "cosine", 0.0))
+    U[g.n_vel // 2] = float("nan")
+    v0 = dev(synth.gaussian_velocity((n, n, n), 1))
+    with pytest.raises(fv.FvError):
+        fv.arnoldi_leading(g, U, v0, m=10, nev=2, prec=prec, max_restarts=2)
+    P = torch.zeros(g.n_cell, dtype=torch.float64, device="cuda")
+    with pytest.raises(fv.FvError):
+        fv.newton_steady(g, U, P, tol=1e-10, prec=prec, max_newton=2)
+    # the grid stays usable
+    U2 = dev(synth.vortex_base_flow((n, n, n), "cosine", 0.0))
+    lam, _ = fv.arnoldi_leading(g, U2, v0, m=20, nev=2, prec=prec, tol=1e-6)
+    assert np.isfinite(np.array(lam)).all()

@@ -94,8 +94,13 @@ __global__ void __launch_bounds__(256, 3) k_dots_pipe(const double* __restrict__
                                                       const VT* __restrict__ V, int64_t ldv,
                                                       int nvec, const double* __restrict__ w,
                                                       int64_t n, double* __restrict__ partial,
-                                                      int al16) {
+                                                      int al16, int vb) {
   static_assert(sizeof(VT) == 8, "8-byte basis entries");
+  // blockIdx.y: the group of vb vectors this block takes (small grids: more
+  // blocks than element chunks); partial[v][blockIdx.x] for its vectors only
+  const int v0 = blockIdx.y * vb;
+  const int v1 = min(nvec, v0 + vb);
+  V += (int64_t)v0 * ldv;
   extern __shared__ __align__(16) unsigned char dsm[];
   VT* ring = (VT*)dsm;
   double* wacc = (double*)(dsm + (size_t)kDotStages * kDotTile * 8);   // [8 warps][kMaxVec]
@@ -105,7 +110,8 @@ __global__ void __launch_bounds__(256, 3) k_dots_pipe(const double* __restrict__
   const int64_t nch = (n + kDotChunk - 1) / kDotChunk;
   const int64_t lo = (nch * blockIdx.x / gridDim.x) * kDotChunk;
   const int64_t hi = blockIdx.x + 1 == gridDim.x ? n : (nch * (blockIdx.x + 1) / gridDim.x) * kDotChunk;
-  const int ntile = nvec * kDotTilesPerChunk;
+  const int nv_ = v1 - v0;
+  const int ntile = nv_ * kDotTilesPerChunk;
   for (int64_t e0 = lo; e0 < hi; e0 += kDotChunk) {
     __syncthreads();                                // the previous chunk is consumed
     const bool full = e0 + kDotChunk <= hi;
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(256, 3) k_dots_pipe(const double* __restrict__
         }
       }
     }
-    for (int v = 0; v < nvec; ++v) {
+    for (int v = 0; v < nv_; ++v) {
       ff sf{0.0f, 0.0f};
       double sd = 0.0;
 #pragma unroll
@@ -196,11 +202,18 @@ __global__ void __launch_bounds__(256, 3) k_dots_pipe(const double* __restrict__
   }
   cpa_wait<0>();
   __syncthreads();
-  for (int v = tid; v < nvec; v += 256) {
+  for (int v = tid; v < nv_; v += 256) {
     double t = 0.0;
     for (int q = 0; q < 8; ++q) t += wacc[q * kMaxVec + v];
-    partial[(int64_t)v * gridDim.x + blockIdx.x] = t;
+    partial[(int64_t)(v0 + v) * gridDim.x + blockIdx.x] = t;
   }
+}
+
+// vectors per block-y group: enough groups that nblk x groups fills three
+// blocks per SM when the element chunks alone do not
+inline int dot_group(int nblk, int nvec) {
+  const int groups = std::max(1, std::min(nvec, kDotBlocks / std::max(1, nblk)));
+  return (nvec + groups - 1) / groups;
 }
 
 __global__ void k_reduce_partials(const double* __restrict__ partial, int nblk,
@@ -471,12 +484,14 @@ fv_status vec_dots(const fv_grid* g, const double* V, int64_t ldv, int nvec, con
   {
     LaunchScope ls_(g, FV_K_DOTS);
     const int al16 = ((uintptr_t)V % 16 == 0) && (ldv % 2 == 0);
+    const int vb = dot_group(nblk, nvec);
+    const dim3 grid(nblk, (nvec + vb - 1) / vb);
     if (ff_arith)
-      k_dots_pipe<true, double><<<nblk, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, V, ldv,
-                                                                  nvec, w, n, g->d_part, al16);
+      k_dots_pipe<true, double><<<grid, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, V, ldv,
+                                                                  nvec, w, n, g->d_part, al16, vb);
     else
-      k_dots_pipe<false, double><<<nblk, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, V, ldv,
-                                                                   nvec, w, n, g->d_part, al16);
+      k_dots_pipe<false, double><<<grid, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, V, ldv,
+                                                                   nvec, w, n, g->d_part, al16, vb);
   }
   FV_CHECK_LAUNCH();
   {
@@ -558,8 +573,10 @@ static fv_status ffb_dots(const fv_grid* g, const float2* Vf, int nvec, const do
   {
     LaunchScope ls_(g, FV_K_DOTS);
     const int al16 = ((uintptr_t)Vf % 16 == 0) && (n % 2 == 0);
-    k_dots_pipe<true, float2><<<nblk, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, Vf, n, nvec,
-                                                                  w, n, g->d_part, al16);
+    const int vb = dot_group(nblk, nvec);
+    const dim3 grid(nblk, (nvec + vb - 1) / vb);
+    k_dots_pipe<true, float2><<<grid, 256, kDotSmem, g->stream>>>(g->wts, g->wts_ff, Vf, n, nvec,
+                                                                  w, n, g->d_part, al16, vb);
   }
   FV_CHECK_LAUNCH();
   {

@@ -49,10 +49,11 @@ __global__ void k_face_weights(Met<double> m, int64_t n, double* __restrict__ W,
 }
 
 // ---- weighted inner products: partial[v][block] = sum over the block's
-// elements of W w V_v.  Each block owns an even, contiguous share of the
-// elements (starting at an even index) and walks it in chunks of kDotChunk,
-// 16 elements per thread: each thread keeps W w of its 16 elements in
-// registers, and the chunk of every V_v streams through a ring of kDotStages
+// elements of W w V_v.  The elements are cut into chunks of kDotChunk (16
+// per thread); block x owns a contiguous run of whole chunks, block y a group
+// of vectors (more than one group only when the chunks alone cannot fill the
+// GPU).  Each thread keeps W w of its 16 elements in registers, and the chunk
+// of every V_v of the group streams through a ring of kDotStages
 // shared-memory tiles of a quarter chunk, filled by asynchronous copies
 // (cp.async; 16 bytes where the basis is 16-byte aligned), so the next tiles
 // are in flight while one is reduced.  FF: float-float products and sums on

@@ -289,6 +289,43 @@ __global__ void __launch_bounds__(256) k_update_ff(double* __restrict__ w,
   }
 }
 
+// k_update_ff for small grids, where one thread per element leaves the GPU
+// mostly idle: 64 elements per block, the vectors split over the block's four
+// thread rows (v = row, row + 4, ...), the four float-float partial sums
+// added in shared memory before w is updated
+template <typename VT>
+__global__ void __launch_bounds__(256) k_update_vsplit(double* __restrict__ w,
+                                                       const VT* __restrict__ V, int64_t ldv,
+                                                       int nvec, const double* __restrict__ h,
+                                                       double sign, int64_t n) {
+  __shared__ float2 hs[kMaxVec];
+  __shared__ float2 part[4][64];
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+    const ff x = f64_split_trunc(sign * h[v]);
+    hs[v] = make_float2(x.hi, x.lo);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+  const int64_t e = (int64_t)blockIdx.x * 64 + tx;
+  ff s{0.0f, 0.0f};
+  if (e < n)
+    for (int v = ty; v < nvec; v += 4) {
+      const float2 c = hs[v];
+      ff_mad(s, ff{c.x, c.y}, to_ff(__ldg(V + (int64_t)v * ldv + e)));
+    }
+  part[ty][tx] = make_float2(s.hi, s.lo);
+  __syncthreads();
+  if (ty == 0 && e < n) {
+    ff t = f64_split_trunc(w[e]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t = ff_add(t, ff{part[q][tx].x, part[q][tx].y});
+    w[e] = ff_join(t.hi, t.lo);
+  }
+}
+
+// grids below this many velocity entries take k_update_vsplit
+constexpr int64_t kUpdateSplitBelow = 1 << 20;
+
 // k_update_ff for a float-float basis, two adjacent elements per thread with
 // 16-byte loads (w, V and ldv 16-byte aligned / even); the odd last element,
 // if any, by the first thread
@@ -509,7 +546,10 @@ fv_status vec_update(const fv_grid* g, double* w, const double* V, int64_t ldv, 
   if (nvec > kMaxVec) { set_error("vec_update: too many vectors"); return FV_EINVAL; }
   {
     LaunchScope ls_(g, FV_K_VECTOR);
-    if (ff_arith)
+    if (ff_arith && g->nvel < kUpdateSplitBelow)
+      k_update_vsplit<double><<<(unsigned)((g->nvel + 63) / 64), 256, 0, g->stream>>>(
+          w, V, ldv, nvec, d_h, sign, g->nvel);
+    else if (ff_arith)
       k_update_ff<double><<<grid1d(g->nvel), 256, 0, g->stream>>>(w, V, ldv, nvec, d_h, sign,
                                                                   g->nvel);
     else
@@ -595,7 +635,10 @@ static fv_status ffb_update(const fv_grid* g, double* w, const float2* Vf, int n
   {
     LaunchScope ls_(g, FV_K_VECTOR);
     const int64_t n = g->nvel;
-    if ((uintptr_t)w % 16 == 0 && (uintptr_t)Vf % 16 == 0 && n % 2 == 0)
+    if (n < kUpdateSplitBelow)
+      k_update_vsplit<float2><<<(unsigned)((n + 63) / 64), 256, 0, g->stream>>>(w, Vf, n, nvec, d_h,
+                                                                              sign, n);
+    else if ((uintptr_t)w % 16 == 0 && (uintptr_t)Vf % 16 == 0 && n % 2 == 0)
       k_update_ffb2<<<grid1d(n / 2 + 1), 256, 0, g->stream>>>(w, Vf, n, nvec, d_h, sign, n);
     else
       k_update_ff<float2><<<grid1d(n), 256, 0, g->stream>>>(w, Vf, n, nvec, d_h, sign, n);

@@ -18,6 +18,7 @@
 #include "fv_ff.cuh"
 #include "fv_internal.cuh"
 #include "fv_stencil_dev.cuh"
+#include "fv_tc5.cuh"
 
 namespace fv {
 
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(256) k_correct_g(MetFF m, const float* __restr
                                                    const CallBlock* __restrict__ cb,
                                                    const LoopState* __restrict__ ls,
                                                    float* __restrict__ part) {
+  tc5::pdl_trigger();   // the pressure transform that follows may start its set-up
   const int done = FIRST ? 0 : ls->pass;
   // result of pass `done` is in vff[(done-1)&1]; the two buffers never overlap
   const float2* __restrict__ vin = (done & 1) ? vff0 : vff1;

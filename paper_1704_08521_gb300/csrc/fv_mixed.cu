@@ -12,6 +12,7 @@
 #include "fv_ff.cuh"
 #include "fv_internal.cuh"
 #include "fv_stencil_dev.cuh"
+#include "fv_tc5.cuh"
 
 namespace fv {
 
@@ -50,6 +51,7 @@ __global__ void k_widen_f32(const float* __restrict__ in, double* __restrict__ o
 // D w in float32 (first residual of the loop; w holds float32 values).
 __global__ void __launch_bounds__(256) k_div_f32(MetFF m, const float* __restrict__ w,
                                                  float* __restrict__ r) {
+  tc5::pdl_trigger();   // the pressure transform that follows may start its set-up
   const int plane_ = m.n[0] * m.n[1];
   const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act_ = t_ < plane_;
@@ -80,6 +82,7 @@ __global__ void __launch_bounds__(256) k_correct_ff(MetFF m, const void* __restr
                                                     const float* __restrict__ phi,
                                                     float2* __restrict__ p, float* __restrict__ r,
                                                     float omega, double* scal) {
+  tc5::pdl_trigger();   // the pressure transform that follows may start its set-up
   const int plane_ = m.n[0] * m.n[1];
   const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act_ = t_ < plane_;
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(256) k_momentum_ff(Met<ffn> m, const float2* _
 // D w of a float-float field, rounded to float32 (first pressure rhs of FV_FF)
 __global__ void __launch_bounds__(256) k_div_ff(MetFF m, const float2* __restrict__ w,
                                                 float* __restrict__ r) {
+  tc5::pdl_trigger();   // the pressure transform that follows may start its set-up
   const int plane_ = m.n[0] * m.n[1];
   const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
   if (t_ >= plane_) return;

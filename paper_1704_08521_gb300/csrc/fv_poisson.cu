@@ -420,10 +420,13 @@ __global__ void __launch_bounds__(kUmmaThreads) k_slab_umma(const float* __restr
   float* Bl = Bh + Nb * Km;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int k = blockIdx.x, a0 = blockIdx.y * Na;
+  tc5::pdl_trigger();
   if (warp == 0) tc5::tmem_alloc(&tslot, tcols);
   if (tid == 0) tc5::mbar_init(&bar, 1);
   // M1 chunk [hi | lo] (128 x K1) -> region A
   stage_pair(bx + (size_t)blockIdx.y * 2 * 128 * K1, Ah, Al, 128 * K1, tid, kUmmaThreads);
+  // everything above uses constants only; the field is the predecessor's output
+  tc5::pdl_wait();
   // the plane (N1 x K1: rows j, columns i) -> Bl in canonical order; a warp
   // pass covers 8 rows x 4 runs (lane: row 8 rb + lane % 8, run 4 kq + lane / 8)
   const float* ink = in + (size_t)k * nx * ny;
@@ -560,9 +563,12 @@ __global__ void __launch_bounds__(kUmmaThreads) k_col_umma(const float* __restri
   const int ldR = N + 4;
   float* R = reinterpret_cast<float*>(nullq + N);   // Kz x ldR raw tile, later transpose scratch
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  tc5::pdl_trigger();
   if (warp == 0) tc5::tmem_alloc(&tslot, tcols);
   if (tid == 0) tc5::mbar_init(&bar, 1);
   stage_pair(azi, Ah, Al, 128 * Kz, tid, kUmmaThreads);
+  // everything above uses constants only; the field is the predecessor's output
+  tc5::pdl_wait();
   // the tile in[kk][q0 .. q0 + N) -> R in 16-byte runs (rows kk >= nz and
   // columns beyond Q zero-filled)
   {
@@ -733,15 +739,36 @@ fv_status set_tc_attributes() {
   return FV_OK;
 }
 
+// Launch with programmatic stream serialization: the kernel's constant
+// set-up (tensor-memory allocation, eigenbasis staging) overlaps the tail of
+// the kernel before it; its pdl_wait() orders every use of that kernel's
+// output.  Captured into the evaluation graphs as a programmatic edge.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // dir 0: forward (Einv) transforms, 1: inverse (E)
 fv_status launch_slab(const fv_grid* g, const float* in, float* out, int dir) {
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   const int N = g->tc.slab_n;
   LaunchScope ls_(g, FV_K_TPF_X);
-  k_slab_umma<<<dim3(nz, g->tc.slab_nsplit), kUmmaThreads, slab_smem(nx, ny, N), g->stream>>>(
-      in, out, g->tc.bx[dir], g->tc.ay[dir], nx, ny, N, tmem_cols(up16(ny) > N ? up16(ny) : N),
-      (nx % 4 == 0 && N % 4 == 0) ? 1 : 0);
-  FV_CHECK_LAUNCH();
+  FV_CUDA(launch_pdl(k_slab_umma, dim3(nz, g->tc.slab_nsplit), dim3(kUmmaThreads),
+                     slab_smem(nx, ny, N), g->stream, in, out, (const float*)g->tc.bx[dir],
+                     (const float*)g->tc.ay[dir], nx, ny, N,
+                     tmem_cols(up16(ny) > N ? up16(ny) : N),
+                     (nx % 4 == 0 && N % 4 == 0) ? 1 : 0));
   return FV_OK;
 }
 
@@ -749,9 +776,10 @@ fv_status launch_col(const fv_grid* g, const float* in, float* out) {
   const int N = g->tc.col_n;
   const int64_t Q = (int64_t)g->n[0] * g->n[1];
   LaunchScope ls_(g, FV_K_TPF_YZ);
-  k_col_umma<<<(unsigned)((Q + N - 1) / N), kUmmaThreads, col_smem(g->n[2], N), g->stream>>>(
-      in, out, g->tpf_f, g->tc.az[0], g->tc.az[1], N, tmem_cols(N), (Q % 4 == 0 && N % 4 == 0) ? 1 : 0);
-  FV_CHECK_LAUNCH();
+  FV_CUDA(launch_pdl(k_col_umma, dim3((unsigned)((Q + N - 1) / N)), dim3(kUmmaThreads),
+                     col_smem(g->n[2], N), g->stream, in, out, g->tpf_f,
+                     (const float*)g->tc.az[0], (const float*)g->tc.az[1], N, tmem_cols(N),
+                     (Q % 4 == 0 && N % 4 == 0) ? 1 : 0));
   return FV_OK;
 }
 

@@ -159,3 +159,21 @@ def test_newton_steady_state_independent_of_the_linear_solver(linear, monkeypatc
     scale = max(float(np.max(np.abs(u))) for u in U0)
     assert max(float(np.max(np.abs(a - c))) for a, c in zip(U0, U1)) <= 1e-9 * scale
     assert h1[-1] < 1e-10 and len(h1) <= len(h0) + 2
+
+
+def test_exact_start_needs_one_product():
+    A, b, w = _system(30, 7)
+    xs = np.linalg.solve(A, b)
+    x, mv, rel = krylov.bicgstab_l(lambda v: A @ v, b, w, x0=xs, l=2, tol=1e-10)
+    assert mv == 1 and rel <= 1e-12
+    np.testing.assert_allclose(x, xs, rtol=0, atol=0)
+
+
+def test_products_cap():
+    # a system that needs many cycles; the cap bounds the operator products
+    A, b, w = _system(150, 8, shift=0.6)
+    x, mv, rel = krylov.bicgstab_l(lambda v: A @ v, b, w, l=2, tol=1e-14, max_iter=41)
+    assert mv <= 41 and mv % 4 == 0
+    x, ng, nb, rel = krylov.gmres_then_bicgstab(lambda v: A @ v, b, w, m=5, tol=1e-14,
+                                                max_iter=60, gmres_sat=0.99)
+    assert ng + nb <= 60 + 5          # GMRES counts a residual per cycle beyond its m steps

@@ -115,7 +115,8 @@ def peaks():
 
 # algorithmic bytes (or flops) of one launch of each kernel class of the
 # mixed path: float32 operands, float-float (8 B) SIMPLE state, float32
-# pressure-correction transforms ("Roofline")
+# pressure-correction transforms: per cell 4 n flop for the two 1-D transforms
+# of a fused launch (2 n each)
 def algorithmic(kind, n, prec):
     cells = n ** 3
     if prec != "mixed":

@@ -13,8 +13,8 @@ def _rand_vel(g, rng):
 @pytest.mark.parametrize("kind", G.MAPS)
 @pytest.mark.parametrize("h", [1.0, 1e-3])
 def test_jacvec_equals_central_difference_of_residual(kind, h):
-    # spec check (a): F is quadratic in U, so the central difference is
-    # exact for any h; the analytic J.v must agree to round-off (<< 1e-6)
+    # F is quadratic in U, so the central difference is exact for any h; the
+    # analytic J.v must agree with it to round-off (<< 1e-6)
     g = G.Grid(5, 6, 7, kind)
     rng = np.random.default_rng(0)
     U, v = _rand_vel(g, rng), _rand_vel(g, rng)
@@ -105,8 +105,8 @@ def test_projection_properties():
 
 @pytest.mark.parametrize("kind", ["uniform", "sine0975", "cosine"])
 def test_second_order_convergence_manufactured(kind):
-    # spec check (c): discrete solution error O(h^2) on a manufactured
-    # steady solution (Newton from rest, Re = 10, all walls at rest)
+    # discrete solution error O(h^2) on a manufactured steady solution
+    # (Newton from rest, Re = 10, all walls at rest)
     pytest.importorskip("sympy")
     re = 10.0
     Uf, Pf, ff = mms.build(re)

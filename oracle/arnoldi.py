@@ -50,27 +50,38 @@ def _keep_count(theta_sorted, k):
 
 
 def _house(x):
-    """Householder vector v (v[0] = 1) and beta with (I - beta v v^T) x = -+||x|| e_1."""
+    """Householder vector v (v[0] = 1) and beta with (I - beta v v^T) x = -+||x|| e_1.
+
+    The reflection maps x onto -sign(x_0) ||x|| e_1, so that v_0 = x_0 - (that
+    value) adds two numbers of the same sign: |v_0| >= |x_0| and every
+    v_i = x_i / v_0 stays below 1 in magnitude (no overflow when x_1.. are
+    tiny next to x_0)."""
     x = np.asarray(x, dtype=np.float64)
-    sigma = float(x[1:] @ x[1:])
-    v = x.copy()
+    v = np.zeros_like(x)
     v[0] = 1.0
-    if sigma == 0.0:
+    if not np.any(x[1:]):
         return v, 0.0
-    mu = np.sqrt(x[0] ** 2 + sigma)
-    v0 = x[0] - mu if x[0] <= 0 else -sigma / (x[0] + mu)
-    beta = 2.0 * v0 ** 2 / (sigma + v0 ** 2)
-    v[1:] = x[1:] / v0
+    s = np.max(np.abs(x))
+    xs = x / s
+    norm = np.sqrt(float(xs @ xs))
+    head = -norm if xs[0] >= 0 else norm          # the image -sign(x_0) ||x||
+    v0 = xs[0] - head
+    v[1:] = xs[1:] / v0
+    beta = (head - xs[0]) / head
     return v, beta
 
 
-def _francis_double_step(H, Q, s, t):
-    """One implicit double-shift QR step on the Hessenberg H for the shifts
-    whose sum is s and product t (Golub & Van Loan, Algorithm 7.5.1);
-    H <- Z^T H Z and Q <- Q Z, in place."""
+def _francis_double_step(H, Q, c, d2):
+    """One implicit double-shift QR step on the Hessenberg H for the shift
+    pair c +- i sqrt(d2) (Golub & Van Loan, Algorithm 7.5.1); H <- Z^T H Z
+    and Q <- Q Z, in place.  The first column of (H - mu_1)(H - mu_2) =
+    (H - c)^2 + d2 is formed from h_00 - c, not from the sum and product of
+    the shifts, whose expansion cancels when H is close to a multiple of
+    the identity."""
     n = H.shape[0]
-    x = H[0, 0] * H[0, 0] + H[0, 1] * H[1, 0] - s * H[0, 0] + t
-    y = H[1, 0] * (H[0, 0] + H[1, 1] - s)
+    a = H[0, 0] - c
+    x = a * a + H[0, 1] * H[1, 0] + d2
+    y = H[1, 0] * (a + H[1, 1] - c)
     z = H[1, 0] * H[2, 1] if n > 2 else 0.0
     for k in range(n - 2):
         v, beta = _house([x, y, z])
@@ -159,7 +170,7 @@ def arnoldi_leading(apply_A, x0, wts, nev=5, m=30, tol=1e-10, max_restarts=2000)
         while i < len(shifts):
             mu = shifts[i]
             if abs(mu.imag) > 0 and i + 1 < len(shifts) and abs(shifts[i + 1] - np.conj(mu)) <= 1e-10 * abs(mu):
-                _francis_double_step(Hs, Q, 2.0 * mu.real, abs(mu) ** 2)
+                _francis_double_step(Hs, Q, mu.real, mu.imag ** 2)
                 i += 2
             else:
                 _single_shift_step(Hs, Q, mu.real)

@@ -46,7 +46,9 @@ typedef enum {
   FV_ECUDA = 3,    /* a CUDA call failed (message in fv_last_error) */
   FV_ENOCONV = 4,  /* an iteration cap was reached */
   FV_ENAN = 5,     /* a NaN/Inf appeared in a norm */
-  FV_ETIMEOUT = 6  /* reserved: a bounded device-side wait gave up */
+  FV_ETIMEOUT = 6  /* a bounded device-side wait gave up (the tensor-core
+                      pressure transforms of FV_MIXED / FV_FF); the grid's
+                      sticky timeout word is cleared once reported */
 } fv_status;
 
 /* Grid stretching.  Section 3, Eq. 5: x -> x - 0.0975 sin(2 pi x) applied to
@@ -110,6 +112,14 @@ typedef struct {
                         [FV_LIN_GMRES_BICGSTAB = 0] */
   double gmres_sat;  /* a GMRES(m) restart cycle whose residual W-norm ends
                         above gmres_sat x its start counts as saturated [0.5] */
+  int precond;       /* 0: the paper's unpreconditioned Krylov vectors; 1: a
+                        Stokes-type right preconditioner M^-1 = P (s - Lap/Re)^-1
+                        (vector Laplacian of the momentum equations, s =
+                        precond_sigma, then the projection onto divergence-free
+                        fields) with flexible GMRES(m) (no BiCGstab(2)
+                        hand-off).  Same corrections; far fewer operator
+                        products on strongly stretched grids              [0] */
+  double precond_sigma; /* s >= 0 of the preconditioner                    [0] */
 } fv_newton_opts;
 
 /* Section 3: the Newton corrections are computed by restarted GMRES or by
@@ -174,6 +184,17 @@ fv_status ns_residual(const fv_grid* g, const double* U, const double* P,
  * arithmetic (inputs and output stay float64). */
 fv_status ns_jacvec(const fv_grid* g, const double* U, const double* v, double* Jv, int prec);
 
+/* Register U[n_vel] as the grid's base flow (Eq. 6: the steady state the
+ * operator is linearised about).  Krylov methods apply the operator about
+ * one U thousands of times; the float32 rounding and float-float split of U
+ * that the FV_MIXED and FV_FF stencils read are made here once instead of in
+ * every evaluation.  Afterwards simple_krylov_solve accepts U = NULL and then
+ * uses these copies (and, for FV_FP64, this array, which the caller keeps
+ * alive and unchanged while it is used that way).  Register again after
+ * changing U.  newton_steady and arnoldi_leading register their U
+ * themselves (this replaces any earlier registration). */
+fv_status fv_grid_set_base(fv_grid* g, const double* U);
+
 /* Section 3, Eqs. 8-10 and the SIMPLE-like algorithm: from v_in compute
  * w = L_U v_in (Eq. 10), then repeat { solve D G phi = D v (Neumann);
  * v -= omega G phi; p += omega phi } until the stop test of opts.  Returns
@@ -181,7 +202,8 @@ fv_status ns_jacvec(const fv_grid* g, const double* U, const double* v, double* 
  * NULL).  v_in and v_out may not alias.  stats may be NULL.
  * FV_MIXED runs the whole evaluation as one CUDA graph launch whose pass
  * loop is decided on the device; the graph is captured on the first such
- * call for a grid (make that call outside any stream capture). */
+ * call for a grid (make that call outside any stream capture).  U = NULL:
+ * the base flow registered by fv_grid_set_base. */
 fv_status simple_krylov_solve(const fv_grid* g, const double* U, const double* v_in,
                               double* v_out, double* p_out,
                               const fv_simple_opts* opts, fv_simple_stats* stats);
@@ -199,7 +221,10 @@ fv_status newton_steady(fv_grid* g, double* U, double* P,
 
 /* Section 3, Eq. 7: the nev (<= 64) eigenvalues of largest real part of the
  * linearised operator about the steady U, by implicitly restarted Arnoldi
- * (Krylov dimension m, nev + 2 <= m <= 128) in regular mode.  v0[n_vel] is
+ * (Krylov dimension m, nev + 2 <= m <= 128) in regular mode.  The Arnoldi
+ * steps of a cycle build the FP64 Hessenberg matrix in device memory with no
+ * host round trip; the small dense restart work (Ritz values by Francis
+ * QR, exact shifts) takes one copy of it per cycle.  v0[n_vel] is
  * the start vector (device; e.g. a seeded Gaussian; it is projected first).
  * lam_re/lam_im (host, nev each) receive the eigenvalues sorted by
  * descending real part, conjugate pairs adjacent (positive imaginary part
@@ -340,19 +365,24 @@ fv_status fv_dot_w(const fv_grid* g, const double* a, const double* b, double* o
 fv_status fv_pressure_solve(const fv_grid* g, const double* r, double* phi, int prec);
 
 /* Allocation-free variant of fv_pressure_solve (prec = FV_MIXED) for callers
- * that cannot allocate device memory -- inside someone else's memory pool,
- * during a CUDA graph capture, or without access to an allocator.  The paper
- * has no counterpart: this is a property of the library, not of the method.
- * It needs no grid handle: nx, ny, nz (each in [4, 128], nx*ny*nz <=
- * 1048576) and map describe the grid; r[n_cell] (device, float64) is the
- * right-hand side, phi[n_cell] (device, float64) receives the zero-mean
- * solution of D G phi = r, work is queued on cuda_stream.  All scratch
- * (eigenbases and two float32 transform buffers, ~8.4 MB) lives in one
- * fixed device array inside the library, allocated when the library is
- * loaded and held by every GPU that loads it until the process exits.  The
- * first call on a device looks up that array's device address (make it
- * before any stream capture).  Sizes beyond the limits give FV_EINVAL.
- * Calls share the array: calls that overlap on the GPU race on it. */
+ * that cannot allocate device memory -- code running inside a memory pool it
+ * does not own and may not grow, or embedded users with no access to an
+ * allocator.  The paper has no counterpart: this is a property of the
+ * library, not of the method.  It needs no grid handle: nx, ny, nz (each in
+ * [4, 128], nx*ny*nz <= 1048576) and map describe the grid; r[n_cell]
+ * (device, float64) is the right-hand side, phi[n_cell] (device, float64)
+ * receives the zero-mean solution of D G phi = r, work is queued on
+ * cuda_stream.  The call makes no cudaMalloc, cudaFree or other allocating
+ * call: all scratch (eigenbases and two float32 transform buffers, ~8.4 MB)
+ * lives in one fixed device array inside the library, which every GPU that
+ * uses it holds until the process exits.  The library's device code is
+ * loaded lazily, so the FIRST call on each device (with that device
+ * current) loads it, reserves the array and looks up its device address:
+ * make that first call before entering any region where the driver may not
+ * reserve memory; later calls reserve nothing.  The host-side tables of
+ * each (dimension, map) are computed on first use and kept.  Sizes beyond
+ * the limits give FV_EINVAL.  Calls share the array: calls that overlap on
+ * the GPU race on it. */
 fv_status fv_pressure_solve_noalloc(int nx, int ny, int nz, int map, const double* r,
                                     double* phi, void* cuda_stream);
 
@@ -367,7 +397,8 @@ typedef enum {
   FV_K_TPF_YZ = 4,     /* pressure solve: y- and z-axis transforms      */
   FV_K_DOTS = 5,       /* weighted inner products                       */
   FV_K_VECTOR = 6,     /* other vector kernels (updates, scaling, ...)  */
-  FV_NKIND = 7
+  FV_K_TPF_XINV = 7,   /* pressure solve: inverse x-y transforms        */
+  FV_NKIND = 8
 } fv_kernel_kind;
 
 /* Start (on != 0) or stop recording; starting clears earlier records. */
@@ -379,9 +410,17 @@ fv_status fv_profile_read(fv_grid* g, double* ms /* host, FV_NKIND */,
 /* Total number of launches (kernel launches and graph launches) this
  * library has issued in the process. */
 int64_t fv_launch_count(void);
+/* Error-path testing without a device fault: set the grid's sticky device
+ * timeout word exactly as a tensor-core pressure transform does when one of
+ * its bounded mbarrier waits gives up, so that the next FV_MIXED / FV_FF
+ * evaluation (or Krylov cycle) on the grid reports FV_ETIMEOUT.  Only
+ * status == FV_ETIMEOUT is accepted (else FV_EINVAL).  Queued on the grid's
+ * stream. */
+fv_status fv_debug_inject_status(fv_grid* g, int status);
 /* Time `reps` back-to-back launches of one FV_MIXED kernel class
- * (FV_K_MOMENTUM, FV_K_DIVERGENCE, FV_K_CORRECT, FV_K_TPF_X, FV_K_TPF_YZ =
- * one z-axis transform) on the grid's workspace with CUDA events on its
+ * (FV_K_MOMENTUM, FV_K_DIVERGENCE, FV_K_CORRECT, FV_K_TPF_X = one forward
+ * x-y slab transform, FV_K_TPF_XINV = one inverse x-y slab transform,
+ * FV_K_TPF_YZ = one z-axis transform) on the grid's workspace with CUDA events on its
  * stream; *ms_per_launch (host) receives the mean device time.  Needs one
  * earlier FV_MIXED simple_krylov_solve on the grid. */
 fv_status fv_bench_kernel(fv_grid* g, int kind, int reps, double* ms_per_launch);

@@ -43,7 +43,8 @@ class fv_newton_opts(ctypes.Structure):
                 ("gmres_max_it", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
                 ("prec", ctypes.c_int), ("sigma", ctypes.c_double),
                 ("simple_eps", ctypes.c_double), ("linear", ctypes.c_int),
-                ("gmres_sat", ctypes.c_double)]
+                ("gmres_sat", ctypes.c_double), ("precond", ctypes.c_int),
+                ("precond_sigma", ctypes.c_double)]
 
 
 class fv_newton_stats(ctypes.Structure):
@@ -110,6 +111,11 @@ class Grid:
     def set_stream(self, stream):
         check(lib.fv_grid_set_stream(self.handle, ctypes.c_void_p(stream)), "fv_grid_set_stream")
 
+    def set_base(self, U):
+        """Register U as the base flow (fv_grid_set_base); evaluations with
+        U=None then use it."""
+        check(lib.fv_grid_set_base(self.handle, _f64(U, self.n_vel, "U")), "fv_grid_set_base")
+
     def info(self):
         i = fv_grid_info()
         check(lib.fv_grid_get_info(self.handle, ctypes.byref(i)), "fv_grid_get_info")
@@ -146,7 +152,8 @@ def simple_krylov_solve(g, U, v_in, v_out, p_out=None, eps=1e-8, max_pass=200, p
                         omega=1.0, sigma=0.0, async_=False):
     o = fv_simple_opts(eps, max_pass, PRECS.get(prec, prec), omega, sigma, 1 if async_ else 0)
     s = fv_simple_stats()
-    check(lib.simple_krylov_solve(g.handle, _f64(U, g.n_vel, "U"), _f64(v_in, g.n_vel, "v_in"),
+    check(lib.simple_krylov_solve(g.handle, None if U is None else _f64(U, g.n_vel, "U"),
+                                  _f64(v_in, g.n_vel, "v_in"),
                                   _f64(v_out, g.n_vel, "v_out"),
                                   None if p_out is None else _f64(p_out, g.n_cell, "p_out"),
                                   ctypes.byref(o), ctypes.byref(s)), "simple_krylov_solve")
@@ -156,9 +163,10 @@ def simple_krylov_solve(g, U, v_in, v_out, p_out=None, eps=1e-8, max_pass=200, p
 
 def newton_steady(g, U, P, tol=1e-10, max_newton=30, gmres_m=100, gmres_max_it=20000,
                   gmres_rtol=1e-8, prec="fp64", sigma=10.0, simple_eps=1e-10, raise_on_fail=True,
-                  linear="gmres+bicgstab", gmres_sat=0.5):
+                  linear="gmres+bicgstab", gmres_sat=0.5, precond=0, precond_sigma=0.0):
     o = fv_newton_opts(tol, max_newton, gmres_m, gmres_max_it, gmres_rtol, PRECS.get(prec, prec),
-                       sigma, simple_eps, LINEAR.get(linear, linear), gmres_sat)
+                       sigma, simple_eps, LINEAR.get(linear, linear), gmres_sat, int(precond),
+                       precond_sigma)
     s = fv_newton_stats()
     st = lib.newton_steady(g.handle, _f64(U, g.n_vel, "U"), _f64(P, g.n_cell, "P"),
                            ctypes.byref(o), ctypes.byref(s))
@@ -231,7 +239,7 @@ def fv_pressure_solve_noalloc(shape, map, r, phi, stream=None):
           "fv_pressure_solve_noalloc")
 
 
-KERNEL_KINDS = ["momentum", "divergence", "correct", "tpf_x", "tpf_yz", "dots", "vector"]
+KERNEL_KINDS = ["momentum", "divergence", "correct", "tpf_x", "tpf_yz", "dots", "vector", "tpf_xinv"]
 
 
 def fv_profile_enable(g, on=True):
@@ -247,6 +255,11 @@ def fv_profile_read(g):
 
 def fv_launch_count():
     return int(lib.fv_launch_count())
+
+
+def fv_debug_inject_status(g, status):
+    """Set the grid's device timeout word as an expired tensor-core wait does."""
+    check(lib.fv_debug_inject_status(g.handle, int(status)), "fv_debug_inject_status")
 
 
 def fv_bench_kernel(g, kind, reps=50):

@@ -33,6 +33,7 @@ _SIGS = {
     "fv_grid_set_re": (_I, [_P, _D]),
     "fv_grid_set_stream": (_I, [_P, _P]),
     "fv_grid_get_info": (_I, [_P, _P]),
+    "fv_grid_set_base": (_I, [_P, _P]),
     "fv_grid_destroy": (None, [_P]),
     "fv_last_error": (ctypes.c_char_p, []),
     "ns_residual": (_I, [_P, _P, _P, _P, _P]),
@@ -65,6 +66,7 @@ _SIGS = {
     "fv_profile_enable": (_I, [_P, _I]),
     "fv_profile_read": (_I, [_P, _P, _P]),
     "fv_launch_count": (ctypes.c_int64, []),
+    "fv_debug_inject_status": (_I, [_P, _I]),
     "fv_bench_kernel": (_I, [_P, _I, _I, _P]),
     "fv_host_hess_eigenvalues": (_I, [_I, _P, _P, _P]),
     "fv_host_shift_steps": (_I, [_I, _P, _P, _I, _P, _P]),

@@ -79,9 +79,22 @@ FF_HD int clz64(uint64_t x) {
 #endif
 }
 
-// d rounded to the nearest float, integer operations only.
+// d rounded to the nearest float, integer operations only.  Values whose
+// float exponent is normal (2^-126 <= |d| < 2^128 before rounding) take a
+// short path: the float's bits are the double's sign, rebiased exponent and
+// top 23 mantissa bits, plus one for round-to-nearest-even (a carry out of
+// the mantissa steps the exponent, up to infinity, as IEEE rounding does);
+// zeros, tiny values, overflow, infinities and NaNs take the general path.
 FF_HD float f64_round_f32(double d) {
   const uint64_t b = bits64(d);
+  const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
+  const uint32_t mag = hw & 0x7fffffffu;
+  if (mag - 0x38100000u < 0x47f00000u - 0x38100000u) {   // double exponent 897 .. 1150
+    uint32_t r = (hw & 0x80000000u) | ((mag - 0x38000000u) << 3) | (lw >> 29);
+    const uint32_t rem = lw & 0x1fffffffu;
+    r += (rem > 0x10000000u) | ((rem == 0x10000000u) & r);
+    return from_bits32(r);
+  }
   const uint32_t sign = (uint32_t)(b >> 63) << 31;
   const int e = (int)((b >> 52) & 0x7ff);
   const uint64_t m = b & 0xfffffffffffffULL;

@@ -2,7 +2,7 @@
 // loop) in the mixed precision of fv_mixed.cu, captured once per grid as a
 // CUDA graph whose pass loop is a device-side WHILE conditional node:
 //
-//   init(call) -> round(U, x) -> J.v -> D w -> [TPF -> correct -> decide]
+//   init(call) -> base(U, if given) -> J.v -> D w -> [TPF -> correct -> decide]
 //   -> while (decide says go on) { TPF -> correct -> decide } -> join
 //
 // The stop test of the loop (||phi_k|| <= eps ||phi_1||, round-off floor,
@@ -13,6 +13,7 @@
 // from a small device block.  The velocity state alternates between two
 // float-float buffers by pass parity, read from the loop state.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 
 #include "fv_ff.cuh"
@@ -24,6 +25,8 @@ namespace fv {
 
 namespace {
 
+// the first two members are read by the J.v kernels as their U and x
+// pointers (U null: the grid's registered base flow)
 struct CallBlock {
   const double* U;
   const double* x;
@@ -44,6 +47,26 @@ __global__ void k_call_init(CallBlock cb, CallBlock* dcb, LoopState* ls) {
   ls->status = 0;
 }
 
+// The evaluation's base flow when the call passes one (U non-null): rounded
+// (FV_MIXED) or split (FV_FF) into the grid's stored copy that the J.v kernel
+// reads; with U null the registered base flow is already there.
+template <bool FF>
+__global__ void k_base_from_call(const CallBlock* __restrict__ cb, float* __restrict__ U32,
+                                 float2* __restrict__ Uff, int64_t n) {
+  const double* U = cb->U;
+  if (!U) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double d = __ldg(U + e);
+    if (FF) {
+      const ff a = f64_split(d);
+      Uff[e] = make_float2(a.hi, a.lo);
+    } else {
+      U32[e] = f64_round_f32(d);
+    }
+  }
+}
+
 __global__ void k_round2(const CallBlock* __restrict__ cb, float* __restrict__ U32,
                          float* __restrict__ x32, int64_t n) {
   const double* U = cb->U;
@@ -52,18 +75,6 @@ __global__ void k_round2(const CallBlock* __restrict__ cb, float* __restrict__ U
        e += (int64_t)gridDim.x * blockDim.x) {
     U32[e] = f64_round_f32(__ldg(U + e));
     x32[e] = f64_round_f32(__ldg(x + e));
-  }
-}
-
-__global__ void k_split2_cb(const CallBlock* __restrict__ cb, float2* __restrict__ Uff,
-                            float2* __restrict__ xff, int64_t n) {
-  const double* U = cb->U;
-  const double* x = cb->x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const ff a = f64_split(__ldg(U + e)), b = f64_split(__ldg(x + e));
-    Uff[e] = make_float2(a.hi, a.lo);
-    xff[e] = make_float2(b.hi, b.lo);
   }
 }
 
@@ -167,7 +178,8 @@ __global__ void __launch_bounds__(256) k_correct_g(MetFF m, const float* __restr
 // cap).  Sets the WHILE condition of the graph.
 __global__ void __launch_bounds__(1024) k_decide(const float* __restrict__ part, int64_t nb,
                                                  LoopState* ls, const CallBlock* __restrict__ cb,
-                                                 cudaGraphConditionalHandle h, int set_handle) {
+                                                 cudaGraphConditionalHandle h, int set_handle,
+                                                 const unsigned* __restrict__ fault) {
   float a = 0.f, d = 0.f;
   for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
     a = fmaxf(a, part[b]);
@@ -185,7 +197,8 @@ __global__ void __launch_bounds__(1024) k_decide(const float* __restrict__ part,
     ls->div_last = d;
     const float phi1 = ls->phi1;
     int go = 1;
-    if (isinf(a) || isinf(d) || isnan(a) || isnan(d)) { ls->nan = 1; ls->status = 3; go = 0; }
+    if (*fault) { ls->status = 4; go = 0; }   // a pressure transform's wait gave up
+    else if (isinf(a) || isinf(d) || isnan(a) || isnan(d)) { ls->nan = 1; ls->status = 3; go = 0; }
     else if (a == 0.f || a <= cb->eps * phi1) { ls->status = 1; go = 0; }
     else if (pass >= 3 && a > 0.25f * prev && a <= 1e-9f * phi1) { ls->status = 1; go = 0; }
     else if (pass >= cb->max_pass) { ls->status = 2; go = 0; }
@@ -226,6 +239,8 @@ inline int block_x(const fv_grid*) { return kCellThreads; }
 
 // Build (once per grid and shift) the executable graph of a mixed-precision
 // Krylov-vector evaluation.
+static_assert(offsetof(CallBlock, U) == 0 && offsetof(CallBlock, x) == sizeof(void*),
+              "the J.v kernels read U and x from the head of the call block");
 static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc, int prec = FV_MIXED) {
   FV_CUDA(cudaMalloc(&gc.d_call, sizeof(CallBlock)));
   FV_CUDA(cudaMalloc((void**)&gc.d_loop, sizeof(LoopState)));
@@ -261,10 +276,11 @@ static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc, int prec 
     k_call_init<<<1, 1, 0, cs>>>(cb0, (CallBlock*)gc.d_call, gc.d_loop);
   }
   if (prec == FV_FF) {
-    // float-float operands and J.v; the predictor lands in vff[1], which the
-    // first (non-initialising) pass reads, with p starting from zero
-    k_split2_cb<<<grid1d(g->nvel), 256, 0, cs>>>(dcb, g->Uff, g->xff, g->nvel);
-    if ((st = launch_momentum_ff(g, g->Uff, g->xff, g->vff[1], sigma)) != FV_OK) return fail(st);
+    // float-float J.v straight from the float64 operands (or the registered
+    // base flow); the predictor lands in vff[1], which the first
+    // (non-initialising) pass reads, with p starting from zero
+    k_base_from_call<true><<<grid1d(g->nvel), 256, 0, cs>>>(dcb, g->U32, g->Uff, g->nvel);
+    if ((st = launch_jv_ff(g, nullptr, nullptr, g->vff[1], sigma, dcb)) != FV_OK) return fail(st);
     if ((st = launch_div_ff(g, g->vff[1], g->r32)) != FV_OK) return fail(st);
     if (cudaMemsetAsync(g->pff, 0, g->ncell * sizeof(float2), cs) != cudaSuccess)
       return fail(cuda_fail(cudaGetLastError(), "cudaMemsetAsync", __FILE__, __LINE__));
@@ -272,8 +288,9 @@ static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc, int prec 
     k_correct_g<false, true><<<cg, bx, 0, cs>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32,
                                                 g->pff, g->r32, dcb, gc.d_loop, part);
   } else {
-    k_round2<<<grid1d(g->nvel), 256, 0, cs>>>(dcb, g->U32, g->x32, g->nvel);
-    if ((st = launch_momentum_f32(g, g->U32, g->x32, g->w32, sigma)) != FV_OK) return fail(st);
+    // float32 J.v straight from the float64 operands (or the registered base)
+    k_base_from_call<false><<<grid1d(g->nvel), 256, 0, cs>>>(dcb, g->U32, g->Uff, g->nvel);
+    if ((st = launch_jv_f32(g, nullptr, nullptr, g->w32, sigma, dcb)) != FV_OK) return fail(st);
     if ((st = launch_div_f32(g, g->w32, g->r32)) != FV_OK) return fail(st);
     if ((st = tpf_solve_f32(g, g->r32, g->phi32)) != FV_OK) return fail(st);
     k_correct_g<true><<<cg, bx, 0, cs>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32, g->pff,
@@ -289,7 +306,7 @@ static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc, int prec 
   cudaGraphConditionalHandle h;
   if (cudaGraphConditionalHandleCreate(&h, cap_graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
     return fail(cuda_fail(cudaGetLastError(), "cudaGraphConditionalHandleCreate", __FILE__, __LINE__));
-  k_decide<<<1, 1024, 0, cs>>>(part, nb, gc.d_loop, dcb, h, 1);
+  k_decide<<<1, 1024, 0, cs>>>(part, nb, gc.d_loop, dcb, h, 1, g->d_fault);
   if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cap_graph, &deps, nullptr, &ndeps) != cudaSuccess)
     return fail(cuda_fail(cudaGetLastError(), "cudaStreamGetCaptureInfo", __FILE__, __LINE__));
   cudaGraphNodeParams cp = {};
@@ -318,7 +335,7 @@ static fv_status build_graph(fv_grid* g, double sigma, GraphCache& gc, int prec 
       else
         k_correct_g<false><<<cg, bx, 0, bs>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32,
                                               g->pff, g->r32, dcb, gc.d_loop, part);
-      k_decide<<<1, 1024, 0, bs>>>(part, nb, gc.d_loop, dcb, h, 1);
+      k_decide<<<1, 1024, 0, bs>>>(part, nb, gc.d_loop, dcb, h, 1, g->d_fault);
     }
     cudaGraph_t bg = body;
     cudaError_t e2 = cudaStreamEndCapture(bs, &bg);
@@ -372,6 +389,7 @@ fv_status mixed_krylov_graph(const fv_grid* gcst, const double* U, const double*
   CallBlock cb;
   cb.U = U;
   cb.x = x;
+  if (U) g->base_ptr = nullptr;   // the graph overwrites the stored base copy
   cb.out = out;
   cb.p = p;
   cb.sigma = (float)sigma;
@@ -399,11 +417,35 @@ fv_status mixed_krylov_graph(const fv_grid* gcst, const double* U, const double*
   if (phil) *phil = hls.phi_last;
   if (divl) *divl = hls.div_last;
   if (status) *status = hls.status;
+  if (hls.status == 4) FV_CUDA(cudaMemset(g->d_fault, 0, sizeof(unsigned)));   // reported once
   return FV_OK;
 }
 
-fv_status graph_take_status(fv_grid* g, int* worst) {
+fv_status take_fault(const fv_grid* g, bool* hit) {
+  unsigned f = 0;
+  FV_CUDA(cudaMemcpyAsync(&f, g->d_fault, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
+  FV_CUDA(cudaMemsetAsync(g->d_fault, 0, sizeof(unsigned), g->stream));
+  FV_CUDA(cudaStreamSynchronize(g->stream));
+  *hit = f != 0;
+  return FV_OK;
+}
+
+fv_status status_error(int status) {
+  switch (status) {
+    case 2: set_error("SIMPLE loop reached max_pass"); return FV_ENOCONV;
+    case 3: set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN;
+    case 4:
+      set_error("pressure transform: a bounded wait on the tensor cores gave up (device timeout)");
+      return FV_ETIMEOUT;
+    default: return FV_OK;
+  }
+}
+
+fv_status graph_take_status(fv_grid* g, int* worst, bool with_fault) {
   *worst = 0;
+  bool hit = false;
+  if (with_fault) FV_TRY(take_fault(g, &hit));
+  if (hit) *worst = 4;
   for (auto& c : g->graphs) {
     if (!c.ready) continue;
     int w = 0;
@@ -437,7 +479,7 @@ fv_status bench_kernel(fv_grid* g, int kind, int reps, double* ms) {
   FV_CUDA(cudaEventCreate(&e1));
   auto one = [&]() -> fv_status {
     switch (kind) {
-      case FV_K_MOMENTUM: return launch_momentum_f32(g, g->U32, g->x32, g->w32, 0.0);
+      case FV_K_MOMENTUM: return launch_jv_f32(g, nullptr, g->vel_buf[1], g->w32, 0.0);
       case FV_K_DIVERGENCE: return launch_div_f32(g, g->w32, g->r32);
       case FV_K_CORRECT:
         count_launch();
@@ -447,6 +489,7 @@ fv_status bench_kernel(fv_grid* g, int kind, int reps, double* ms) {
         FV_CHECK_LAUNCH();
         return FV_OK;
       case FV_K_TPF_X: return tpf_one_transform_f32(g, 0);
+      case FV_K_TPF_XINV: return tpf_one_transform_f32(g, 1);
       case FV_K_TPF_YZ: return tpf_one_transform_f32(g, 2);
       default: set_error("fv_bench_kernel: unsupported kind"); return FV_EINVAL;
     }
@@ -711,7 +754,7 @@ static fv_status batch_build_graph(BatchImpl& b) {
     BCHK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cap, &deps, nullptr, &nd));
     cudaGraphConditionalHandle h;
     BCHK(cudaGraphConditionalHandleCreate(&h, cap, 1, cudaGraphCondAssignDefault));
-    k_decide<<<1, 1024, 0, s>>>(part, nb, dls, dcb, h, 1);
+    k_decide<<<1, 1024, 0, s>>>(part, nb, dls, dcb, h, 1, g->d_fault);
     BCHK(cudaGetLastError());
     BCHK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cap, &deps, nullptr, &nd));
     cudaGraphNodeParams cp = {};
@@ -729,7 +772,7 @@ static fv_status batch_build_graph(BatchImpl& b) {
     if (s2 == FV_OK) {
       k_correct_g<false><<<cg, bx, 0, bs[i]>>>(g->met_ff, g->w32, g->vff[0], g->vff[1], g->phi32,
                                                g->pff, g->r32, dcb, dls, part);
-      k_decide<<<1, 1024, 0, bs[i]>>>(part, nb, dls, dcb, h, 1);
+      k_decide<<<1, 1024, 0, bs[i]>>>(part, nb, dls, dcb, h, 1, g->d_fault);
     }
     cudaGraph_t bg = body;
     cudaError_t e2 = cudaStreamEndCapture(bs[i], &bg);
@@ -852,6 +895,9 @@ fv_status fv_batch_krylov(fv_batch* b, const double* const* U, const double* con
   kp.blockDim = dim3(kBatchMax);
   kp.kernelParams = args;
   FV_CUDA(cudaGraphExecKernelNodeSetParams(B.exec, B.init_node, &kp));
+  // the batch rounds each instance's U into the grid's U32, replacing a
+  // base flow registered on that grid
+  for (int i = 0; i < B.n; ++i) B.grids[i]->base_ptr = nullptr;
   count_launch();
   FV_CUDA(cudaGraphLaunch(B.exec, B.stream));
   if (passes) {
@@ -860,11 +906,16 @@ fv_status fv_batch_krylov(fv_batch* b, const double* const* U, const double* con
                             B.stream));
     FV_CUDA(cudaStreamSynchronize(B.stream));
     for (int i = 0; i < B.n; ++i) passes[i] = h[i].pass;
-    for (int i = 0; i < B.n; ++i)
-      if (h[i].status != 1) {
-        set_error("fv_batch_krylov: an instance did not converge");
-        return h[i].status == 3 ? FV_ENAN : FV_ENOCONV;
-      }
+    int worst = 1;
+    for (int i = 0; i < B.n; ++i) {
+      if (h[i].status == 4) FV_CUDA(cudaMemsetAsync(B.grids[i]->d_fault, 0, sizeof(unsigned), B.stream));
+      worst = std::max(worst, h[i].status == 0 ? 2 : h[i].status);
+    }
+    if (worst != 1) {
+      const fv_status e = status_error(worst);
+      set_error(std::string("fv_batch_krylov: an instance did not converge: ") + fv_last_error());
+      return e;
+    }
   }
   return FV_OK;
 }

@@ -1,6 +1,7 @@
 // Grid construction: stretched face coordinates (Section 3, Eq. 5), the
 // finite-volume metrics, the tensor-product eigenbases of the pressure-
 // correction operator (the TPF idea of Section 3) and all workspace.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -10,6 +11,7 @@
 
 #include "fv_ff.cuh"
 #include "fv_internal.cuh"
+#include "fvns_host.h"
 
 namespace fv {
 
@@ -118,6 +120,11 @@ static bool tridiag_eig(int n, const std::vector<double>& d, const std::vector<d
   lam.resize(n);
   for (int i = 0; i < n; ++i) lam[i] = a(i, i);
   return true;
+}
+
+bool sym_tridiag_eig(int n, const std::vector<double>& d, const std::vector<double>& e,
+                     std::vector<double>& lam, std::vector<double>& Z) {
+  return tridiag_eig(n, d, e, lam, Z);
 }
 
 // Neumann operator of one axis, L = dx^{-1} T, T symmetric tridiagonal
@@ -349,6 +356,8 @@ static fv_status build(fv_grid* g) {
   FV_TRY(alloc(g, (void**)&g->Uff, g->nvel * sizeof(float2)));
   FV_TRY(alloc(g, (void**)&g->xff, g->nvel * sizeof(float2)));
   FV_TRY(alloc(g, (void**)&g->d_scal, kScalars * sizeof(double)));
+  FV_TRY(alloc(g, (void**)&g->d_fault, 256));
+  FV_CUDA(cudaMemset(g->d_fault, 0, 256));
   g->part_len = 4096 * 130;
   FV_TRY(alloc(g, (void**)&g->d_part, g->part_len * sizeof(double)));
   FV_TRY(alloc(g, (void**)&g->wts, g->nvel * sizeof(double)));
@@ -452,15 +461,32 @@ fv_status fv_profile_read(fv_grid* g, double* ms, int64_t* launches) {
 
 int64_t fv_launch_count(void) { return g_launches.load(); }
 
+fv_status fv_grid_set_base(fv_grid* g, const double* U) {
+  if (!g || !U) { set_error("fv_grid_set_base: NULL argument"); return FV_EINVAL; }
+  return set_base(g, U);
+}
+
+fv_status fv_debug_inject_status(fv_grid* g, int status) {
+  if (!g) { set_error("fv_debug_inject_status: NULL grid"); return FV_EINVAL; }
+  if (status != FV_ETIMEOUT) {
+    set_error("fv_debug_inject_status: only FV_ETIMEOUT can be injected");
+    return FV_EINVAL;
+  }
+  FV_CUDA(cudaMemsetAsync(g->d_fault, 0x01, 1, g->stream));
+  return FV_OK;
+}
+
 void fv_grid_destroy(fv_grid* g) {
   if (!g) return;
   for (auto& c : g->graphs) destroy_graph_cache(c);
+  destroy_stokes_tables(g);
+  if (g->d_arn) cudaFree(g->d_arn);
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   void* ptrs[] = {g->d_met_d, g->d_met_f, g->d_tpf_d, g->d_tpf_f, g->vel_buf[0], g->vel_buf[1],
                   g->vel_buf[2], g->cell_buf[0], g->cell_buf[1], g->cell_buf[2], g->tpf_buf[0],
                   g->tpf_buf[1], g->d_scal, g->d_part, g->kry, g->kry_small, g->U32, g->x32,
                   g->w32, g->vff[0], g->vff[1], g->pff, g->r32, g->phi32, g->d_met_ff,
-                  g->d_met_fn, g->Uff, g->xff, g->d_tc, g->wts, g->wts_ff};
+                  g->d_met_fn, g->Uff, g->xff, g->d_tc, g->wts, g->wts_ff, g->d_fault};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_scal) cudaFreeHost(g->h_scal);

@@ -98,7 +98,8 @@ struct TcMats {
 // device-side state of one SIMPLE loop (graph path)
 struct LoopState {
   float phi1, phi_prev, phi_last, div_last;
-  int pass, nan, status;        // status: 0 running, 1 converged, 2 pass cap, 3 NaN
+  int pass, nan, status;        // status: 0 running, 1 converged, 2 pass cap, 3 NaN,
+                                // 4 a bounded wait of a pressure transform gave up
   int worst;                    // largest status of the evaluations since graph_take_status
                                 // (kept across evaluations: lets drivers launch them
                                 // asynchronously and check once per cycle)
@@ -146,6 +147,7 @@ struct fv_grid {
   double* cell_buf[3] = {nullptr, nullptr, nullptr};  // n_cell each
   void* tpf_buf[2] = {nullptr, nullptr};              // n_cell doubles each (float use half)
   double* d_scal = nullptr;      // 64 device scalars
+  unsigned* d_fault = nullptr;   // sticky: nonzero once a bounded device wait gave up
   double* d_part = nullptr;      // reduction partials
   double* wts = nullptr;         // W: momentum control-volume size per velocity entry
   float2* wts_ff = nullptr;      // W split into float-float pairs
@@ -168,6 +170,9 @@ struct fv_grid {
   fv::Met<fv::ffn> met_fn;
   float2* Uff = nullptr;         // n_vel
   float2* xff = nullptr;         // n_vel
+  // registered base flow (fv_grid_set_base): U32 / Uff hold its rounding and
+  // split, base_ptr the caller's float64 array (used by the FP64 form)
+  const double* base_ptr = nullptr;
 
   // captured evaluation graphs of the mixed path (built on first use)
   fv::GraphCache graphs[4];
@@ -180,10 +185,17 @@ struct fv_grid {
   mutable std::vector<int> ev_kind;     // kind of each recorded (start, stop) pair
   mutable size_t ev_used = 0;
 
+  // Stokes preconditioner of the Newton corrections (built on first use)
+  void* d_helm = nullptr;        // per axis: face and cell eigenbases, scaled eigenvalues
+  fv::TpfDev<float> helm[3];     // per velocity component
+  std::vector<double> helm_lam[3][2];   // raw 1-D eigenvalues per axis (0 face, 1 cell)
+  double helm_sigma = -1.0, helm_re = -1.0;
+
   // Krylov basis (allocated on first use)
   double* kry = nullptr;
   int kry_cols = 0;
   double* kry_small = nullptr;   // device small-matrix area
+  void* d_arn = nullptr;         // device Arnoldi area: the cycle's Hessenberg H, a scale
 };
 
 namespace fv {
@@ -237,8 +249,17 @@ fv_status launch_correct_div(const fv_grid* g, const double* vin, double* vout,
 fv_status launch_zero_walls(const fv_grid* g, double* v);
 
 // mixed-precision path (fv_mixed.cu)
-fv_status launch_momentum_f32(const fv_grid* g, const float* U32, const float* v32, float* out,
+// J.v tiled kernels (fv_jv.cuh): U from Ud (float64) or, when null, the
+// grid's registered base flow (U32 / Uff); x float64; call (graph launches):
+// a device block whose first two members are the U and x pointers
+fv_status launch_jv_f32(const fv_grid* g, const double* Ud, const double* x, float* out,
+                        double shift, const void* call = nullptr);
+fv_status launch_jv_f32_out64(const fv_grid* g, const double* Ud, const double* x, double* out,
                               double shift);
+fv_status launch_jv_ff(const fv_grid* g, const double* Ud, const double* x, float2* out,
+                       double shift, const void* call = nullptr);
+fv_status launch_jv_ff_out64(const fv_grid* g, const double* Ud, const double* x, double* out,
+                             double shift);
 fv_status launch_round_f32(const fv_grid* g, const double* in, float* out, int64_t n);
 fv_status launch_div_f32(const fv_grid* g, const float* w32, float* r32);
 // one float-float SIMPLE pass; first: vin is the float32 w, p starts at 0
@@ -252,8 +273,8 @@ fv_status launch_widen_f32(const fv_grid* g, const float* in, double* out, int64
 
 // FV_FF operands and stencil (fv_mixed.cu)
 fv_status launch_split_ff(const fv_grid* g, const double* in, float2* out, int64_t n);
-fv_status launch_momentum_ff(const fv_grid* g, const float2* U, const float2* v, float2* out,
-                             double shift);
+// register U as the grid's base flow: U32 = round(U), Uff = split(U)
+fv_status set_base(fv_grid* g, const double* U);
 fv_status launch_div_ff(const fv_grid* g, const float2* w, float* r32);
 
 // graph path (fv_graph.cu): one mixed-precision Krylov-vector evaluation as
@@ -267,17 +288,34 @@ void destroy_graph_cache(GraphCache& c);
 // tensor-product pressure solve: phi = (D G)^+ r ; phi is float or double
 fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec);
 fv_status tpf_solve_f32(const fv_grid* g, const float* r, float* phi);
+// the unfused float32 transforms with the tables and eigenvalues of tp
+// (scaling by 1 / (lam_z + lam_y + lam_x); null_index -1: no null mode)
+fv_status tpf_run_f32(const fv_grid* g, const TpfDev<float>& tp, const float* r, float* phi);
+// right preconditioner of the Newton corrections (fv_precond.cu):
+// out = P (sigma_p - Lap / Re)^-1 y, float32 transforms, float-float projection
+fv_status stokes_precond_apply(fv_grid* g, const double* y, double* out, double sigma_p);
+// out = P (g->w32): the mixed SIMPLE loop from the float32 field in g->w32
+// (divergence in g->r32) to a relative correction eps (fv_krylov.cu)
+fv_status simple_project_w32(const fv_grid* g, double* out, double eps);
+void destroy_stokes_tables(fv_grid* g);
 // builds g->tc when every dimension is <= 128 (fv_poisson.cu)
 fv_status build_tc_mats(fv_grid* g);
+
 // learned first pass of the SIMPLE loop (fv_unet.cu): phi = guess for r
 fv_status unet_guess_f32(fv_unet* u, const fv_grid* g, const float* r, float* phi);
 // max |x[0..n)| of a float32 array to the host (synchronises g's stream)
 fv_status absmax_f32_host(const fv_grid* g, const float* x, int64_t n, double* out);
 fv_status tpf_one_transform_f32(const fv_grid* g, int axis);
 
-// the largest status (1 converged, 2 pass cap, 3 NaN; 0 none) of the graph
-// evaluations on g since the last call, then reset (synchronises g's stream)
-fv_status graph_take_status(fv_grid* g, int* worst);
+// the largest status (1 converged, 2 pass cap, 3 NaN, 4 timeout; 0 none) of
+// the graph evaluations on g since the last call, then reset (synchronises
+// g's stream); with_fault = false leaves the sticky timeout word alone (it
+// stays pending until an evaluation reports it)
+fv_status graph_take_status(fv_grid* g, int* worst, bool with_fault = true);
+// read and clear g's sticky timeout word (synchronises g's stream)
+fv_status take_fault(const fv_grid* g, bool* hit);
+// the fv_status of an evaluation status (0/1 -> FV_OK) with its message
+fv_status status_error(int status);
 // fill g->wts and g->wts_ff (the W of the inner products; 0 on wall faces)
 fv_status fill_face_weights(fv_grid* g);
 // vector kernels (weighted inner products, Gram-Schmidt); ff_arith: the
@@ -306,6 +344,11 @@ double bits_to_double(double slot);
 // H is m x m row-major upper Hessenberg.
 bool hess_eigenvalues(int m, const double* H, double* wr, double* wi);
 bool host_axis_tables(int n, int map, AxisBasis& B);
+// eigen-decomposition of the symmetric tridiagonal (d, e): lam, Z (n x n
+// row-major, eigenvectors as columns); implicit QR with Wilkinson shifts
+bool sym_tridiag_eig(int n, const std::vector<double>& d, const std::vector<double>& e,
+                     std::vector<double>& lam, std::vector<double>& Z);
+
 // one implicit double-shift step with the shift pair re +- i im (Q accumulated)
 void francis_double_step(int m, double* H, double* Q, double re, double im);
 void single_shift_step(int m, double* H, double* Q, double mu);

@@ -602,6 +602,74 @@ fv_status vec_combine(const fv_grid* g, const double* V, int64_t ldv, int nin, c
   return FV_OK;
 }
 
+// Gram-Schmidt step of a device-resident Arnoldi cycle: column j of H gets
+// h_i = (first + second CGS pass coefficients) for i < j1 and the norm of the
+// new vector at row j1 (sub_only: the norm alone); *scale = 1 / norm.
+__global__ void k_gs_finish(const double* __restrict__ dh1, const double* __restrict__ dh2,
+                            const double* __restrict__ dnn, int j1, double* __restrict__ Hcol, int ld,
+                            double* __restrict__ scale, int sub_only) {
+  if (!sub_only)
+    for (int i = threadIdx.x; i < j1; i += blockDim.x) Hcol[(int64_t)i * ld] = dh1[i] + dh2[i];
+  if (threadIdx.x == 0) {
+    const double hn = sqrt(fmax(dnn[0], 0.0));
+    Hcol[(int64_t)j1 * ld] = hn;
+    scale[0] = hn > 0.0 ? 1.0 / hn : 0.0;
+  }
+}
+
+__global__ void k_store_ff_dev(int64_t n, const double* __restrict__ x, const double* __restrict__ scale,
+                               float2* __restrict__ col) {
+  const double sc = scale[0];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const ff s = f64_split_trunc(sc * x[e]);
+    col[e] = make_float2(s.hi, s.lo);
+  }
+}
+
+// entry of largest modulus of the complex vector (re, im): per-block
+// (value, index) partials, then one block reduces them and writes
+// out[0] = re[big], out[1] = im[big]
+__global__ void k_absmax_c(int64_t n, const double* __restrict__ re, const double* __restrict__ im,
+                           double* __restrict__ pv, int64_t* __restrict__ pi) {
+  __shared__ double sv[256];
+  __shared__ int64_t si[256];
+  double bv = -1.0;
+  int64_t bi = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = re[e] * re[e] + im[e] * im[e];
+    if (v > bv) { bv = v; bi = e; }
+  }
+  sv[threadIdx.x] = bv;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double o = sv[threadIdx.x + s];
+      const int64_t oi = si[threadIdx.x + s];
+      if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+        sv[threadIdx.x] = o;
+        si[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { pv[blockIdx.x] = sv[0]; pi[blockIdx.x] = si[0]; }
+}
+
+__global__ void k_absmax_c_final(int nb, const double* __restrict__ pv, const int64_t* __restrict__ pi,
+                                 const double* __restrict__ re, const double* __restrict__ im,
+                                 double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double bv = -1.0;
+  int64_t bi = 0;
+  for (int b = 0; b < nb; ++b)
+    if (pv[b] > bv || (pv[b] == bv && pi[b] < bi)) { bv = pv[b]; bi = pi[b]; }
+  out[0] = re[bi];
+  out[1] = im[bi];
+}
+
 // ---- a Krylov basis stored as float-float pairs (the mixed and float-float
 // Arnoldi bases): each vector is split once when it is stored, so the
 // Gram-Schmidt kernels read (hi, lo) pairs instead of splitting doubles
@@ -806,6 +874,9 @@ static fv_status simple_loop_ff(const fv_grid* g, double* out, double* p_out, co
     nxt ^= 1;
     FV_TRY(fetch_scalars(g, h));
     res->passes = pass;
+    bool timed_out = false;
+    FV_TRY(take_fault(g, &timed_out));
+    if (timed_out) return status_error(4);
     if (h[S_NAN] != 0.0) { set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN; }
     const double ph = slot_float(h, S_PHI_MAX_F);
     res->div_max = slot_float(h, S_DIV_MAX_F);
@@ -826,6 +897,13 @@ static fv_status simple_loop_ff(const fv_grid* g, double* out, double* p_out, co
   return st;
 }
 
+// out = P w32 (the float32 field in g->w32, whose divergence is in g->r32):
+// the mixed SIMPLE loop without a predictor, to a relative correction eps
+fv_status simple_project_w32(const fv_grid* g, double* out, double eps) {
+  SimpleResult r;
+  return simple_loop_ff(g, out, nullptr, nullptr, 0.0, eps, 50, 1.0, &r);
+}
+
 // A_sigma x = P (L_U x + sigma x) - sigma x  (sigma = 0: the Krylov vector).
 // out must not alias x.  Uses vel_buf[0] as scratch.
 static fv_status krylov_apply(const fv_grid* g, const double* U, const double* x, double* out,
@@ -838,24 +916,18 @@ static fv_status krylov_apply(const fv_grid* g, const double* U, const double* x
                                 res ? &res->passes : nullptr, res ? &res->phi_first : nullptr,
                                 res ? &res->phi_last : nullptr, res ? &res->div_max : nullptr,
                                 &status, prec));
-      if (res && status == 3) { set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN; }
-      if (res && status == 2) { set_error("SIMPLE loop reached max_pass"); return FV_ENOCONV; }
-      return FV_OK;
+      return res ? status_error(status) : FV_OK;
     }
     if (prec == FV_FF) {
-      FV_TRY(launch_split_ff(g, U, g->Uff, g->nvel));
-      FV_TRY(launch_split_ff(g, x, g->xff, g->nvel));
-      FV_TRY(launch_momentum_ff(g, g->Uff, g->xff, g->vff[1], sigma));
+      FV_TRY(launch_jv_ff(g, U, x, g->vff[1], sigma));
       FV_TRY(launch_div_ff(g, g->vff[1], g->r32));
       return simple_loop_ff(g, out, p, x, sigma, eps, max_pass, omega, res, true);
     }
-    FV_TRY(launch_round_f32(g, U, g->U32, g->nvel));
-    FV_TRY(launch_round_f32(g, x, g->x32, g->nvel));
-    FV_TRY(launch_momentum_f32(g, g->U32, g->x32, g->w32, sigma));
+    FV_TRY(launch_jv_f32(g, U, x, g->w32, sigma));
     FV_TRY(launch_div_f32(g, g->w32, g->r32));
     return simple_loop_ff(g, out, p, x, sigma, eps, max_pass, omega, res);
   }
-  FV_TRY(launch_momentum_jac(g, U, x, out, prec, sigma));
+  FV_TRY(launch_momentum_jac(g, U ? U : g->base_ptr, x, out, prec, sigma));
   fv_status s = simple_loop(g, out, g->vel_buf[0], out, p, eps, max_pass, prec, omega, res);
   if (s != FV_OK) return s;
   if (sigma != 0.0) FV_TRY(vec_axpby(g, g->nvel, 1.0, out, -sigma, x, out));
@@ -873,9 +945,7 @@ static fv_status check_products(const fv_grid* gc, int prec) {
   if (!(g->use_graph && (prec == FV_MIXED || prec == FV_FF))) return FV_OK;
   int w = 0;
   FV_TRY(graph_take_status(g, &w));
-  if (w == 3) { set_error("SIMPLE loop: NaN/Inf in the correction"); return FV_ENAN; }
-  if (w == 2) { set_error("SIMPLE loop reached max_pass"); return FV_ENOCONV; }
-  return FV_OK;
+  return status_error(w);
 }
 
 // Project x in place onto divergence-free fields (p: optional pressure out),
@@ -943,6 +1013,50 @@ static fv_status cgs2_ffb(const fv_grid* g, const float2* Vf, int j1, double* w,
   FV_CUDA(cudaStreamSynchronize(g->stream));
   for (int i = 0; i < j1; ++i) h_host[i] = tmp[i] + tmp[kMaxVec + i];
   *wnorm = std::sqrt(std::max(tmp[2 * kMaxVec], 0.0));
+  return FV_OK;
+}
+
+// CGS2 of w against the first j1 basis vectors (float-float basis Vf, or the
+// FP64 basis V), the coefficients and the norm written into column `Hcol` of
+// the device Hessenberg (leading dimension ld) by k_gs_finish, *dscale =
+// 1 / norm: nothing returns to the host
+static fv_status cgs2_dev(const fv_grid* g, const float2* Vf, const double* V, int j1, double* w,
+                          double* Hcol, int ld, double* dscale, bool sub_only) {
+  double* dh1 = g->kry_small;
+  double* dh2 = g->kry_small + kMaxVec;
+  double* dnn = g->kry_small + 2 * kMaxVec;
+  if (Vf) {
+    FV_TRY(ffb_dots(g, Vf, j1, w, dh1));
+    FV_TRY(ffb_update(g, w, Vf, j1, dh1, -1.0));
+    FV_TRY(ffb_dots(g, Vf, j1, w, dh2));
+    FV_TRY(ffb_update(g, w, Vf, j1, dh2, -1.0));
+    FV_TRY(vec_dots(g, w, g->nvel, 1, w, dnn, true));
+  } else {
+    FV_TRY(vec_dots(g, V, g->nvel, j1, w, dh1, false));
+    FV_TRY(vec_update(g, w, V, g->nvel, j1, dh1, -1.0, false));
+    FV_TRY(vec_dots(g, V, g->nvel, j1, w, dh2, false));
+    FV_TRY(vec_update(g, w, V, g->nvel, j1, dh2, -1.0, false));
+    FV_TRY(vec_dots(g, w, g->nvel, 1, w, dnn, false));
+  }
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    k_gs_finish<<<1, 128, 0, g->stream>>>(dh1, dh2, dnn, j1, Hcol, ld, dscale, sub_only ? 1 : 0);
+  }
+  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+// store w / norm (device scale) as basis column `col`
+static fv_status store_scaled(const fv_grid* g, const double* w, const double* dscale, float2* colf,
+                              double* cold) {
+  {
+    LaunchScope ls_(g, FV_K_VECTOR);
+    if (colf)
+      k_store_ff_dev<<<grid1d(g->nvel), 256, 0, g->stream>>>(g->nvel, w, dscale, colf);
+    else
+      k_scale_dev<<<grid1d(g->nvel), 256, 0, g->stream>>>(g->nvel, w, dscale, 1, cold);
+  }
+  FV_CHECK_LAUNCH();
   return FV_OK;
 }
 
@@ -1095,12 +1209,7 @@ fv_status ns_jacvec(const fv_grid* g, const double* U, const double* v, double* 
   if (!U || !v || !Jv) { set_error("ns_jacvec: NULL pointer"); return FV_EINVAL; }
   if (prec != FV_FP64 && prec != FV_MIXED && prec != FV_FF) { set_error("ns_jacvec: bad prec"); return FV_EINVAL; }
   if (v == Jv || U == Jv) { set_error("ns_jacvec: output aliases an input"); return FV_EINVAL; }
-  if (prec == FV_FF) {
-    FV_TRY(launch_split_ff(g, U, g->Uff, g->nvel));
-    FV_TRY(launch_split_ff(g, v, g->xff, g->nvel));
-    FV_TRY(launch_momentum_ff(g, g->Uff, g->xff, g->vff[1], 0.0));
-    return launch_join_ff(g, g->vff[1], nullptr, 0.0, Jv, g->nvel);
-  }
+  if (prec == FV_FF) return launch_jv_ff_out64(g, U, v, Jv, 0.0);
   return launch_momentum_jac(g, U, v, Jv, prec, 0.0);
 }
 
@@ -1113,7 +1222,11 @@ fv_status fv_dot_w(const fv_grid* g, const double* a, const double* b, double* o
 fv_status simple_krylov_solve(const fv_grid* g, const double* U, const double* v_in, double* v_out,
                               double* p_out, const fv_simple_opts* opts, fv_simple_stats* stats) {
   FV_TRY(check_grid(g, "simple_krylov_solve"));
-  if (!U || !v_in || !v_out) { set_error("simple_krylov_solve: NULL pointer"); return FV_EINVAL; }
+  if (!v_in || !v_out) { set_error("simple_krylov_solve: NULL pointer"); return FV_EINVAL; }
+  if (!U && !g->base_ptr) {
+    set_error("simple_krylov_solve: U is NULL and no base flow is registered (fv_grid_set_base)");
+    return FV_EINVAL;
+  }
   if (v_in == v_out) { set_error("simple_krylov_solve: v_in and v_out alias"); return FV_EINVAL; }
   fv_simple_opts o = {};
   if (opts) o = *opts;
@@ -1155,16 +1268,12 @@ fv_status simple_krylov_solve_guess(const fv_grid* g, fv_unet* u, const double* 
   SimpleResult r;
   fv_status s;
   if (o.prec == FV_FF) {
-    FV_TRY(launch_split_ff(g, U, g->Uff, g->nvel));
-    FV_TRY(launch_split_ff(g, v_in, g->xff, g->nvel));
-    FV_TRY(launch_momentum_ff(g, g->Uff, g->xff, g->vff[1], o.sigma));
+    FV_TRY(launch_jv_ff(g, U, v_in, g->vff[1], o.sigma));
     FV_TRY(launch_div_ff(g, g->vff[1], g->r32));
     FV_TRY(unet_guess_f32(u, g, g->r32, g->phi32));
     s = simple_loop_ff(g, v_out, p_out, v_in, o.sigma, o.eps, o.max_pass, o.omega, &r, true, g->phi32);
   } else {
-    FV_TRY(launch_round_f32(g, U, g->U32, g->nvel));
-    FV_TRY(launch_round_f32(g, v_in, g->x32, g->nvel));
-    FV_TRY(launch_momentum_f32(g, g->U32, g->x32, g->w32, o.sigma));
+    FV_TRY(launch_jv_f32(g, U, v_in, g->w32, o.sigma));
     FV_TRY(launch_div_f32(g, g->w32, g->r32));
     FV_TRY(unet_guess_f32(u, g, g->r32, g->phi32));
     s = simple_loop_ff(g, v_out, p_out, v_in, o.sigma, o.eps, o.max_pass, o.omega, &r, false, g->phi32);
@@ -1205,14 +1314,21 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     set_error("newton_steady: bad option (gmres_m <= 128, prec, linear)");
     return FV_EINVAL;
   }
+  if (o.precond < 0 || o.precond > 1 || o.precond_sigma < 0.0) {
+    set_error("newton_steady: bad option (precond 0 or 1, precond_sigma >= 0)");
+    return FV_EINVAL;
+  }
+  const bool pre = o.precond == 1;
+  if (pre) o.linear = FV_LIN_GMRES;            // flexible GMRES(m) with the stored M^-1 v_j
   const int m = o.gmres_m;
-  FV_TRY(ensure_krylov(g, std::max(m + 1, 8)));
+  FV_TRY(ensure_krylov(g, pre ? 2 * m + 1 : std::max(m + 1, 8)));
   {
     int w;                                     // forget statuses of earlier evaluations
-    FV_TRY(graph_take_status(g, &w));
+    FV_TRY(graph_take_status(g, &w, false));
   }
   const int64_t nv = g->nvel;
   double* V = g->kry;
+  double* Z = pre ? g->kry + (int64_t)(m + 1) * nv : nullptr;   // preconditioned directions
   double* Fm = g->vel_buf[1];
   double* du = g->vel_buf[2];
   fv_newton_stats st = {};
@@ -1273,6 +1389,8 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     if (cur_prec == FV_MIXED && prev_res > 0.0 && res > 0.1 * prev_res) cur_prec = FV_FP64;
     prev_res = res;
     const double lin_rtol = cur_prec == FV_MIXED ? std::max(o.gmres_rtol, 1e-6) : o.gmres_rtol;
+    // the Jacobian of this step: U converted once for all its Krylov vectors
+    NT_TRY(set_base(g, U));
 
     // GMRES(m) for A_sigma du = Fm, du = 0 initially
     NT_CUDA(cudaMemsetAsync(du, 0, nv * sizeof(double), g->stream));
@@ -1289,7 +1407,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       if (first) {
         NT_CUDA(cudaMemcpyAsync(V, Fm, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
       } else {
-        NT_TRY(krylov_apply(g, U, du, V, nullptr, o.sigma, cur_prec, o.simple_eps, 200, 1.0,
+        NT_TRY(krylov_apply(g, nullptr, du, V, nullptr, o.sigma, cur_prec, o.simple_eps, 200, 1.0,
                             nullptr));
         NT_TRY(vec_axpby(g, nv, -1.0, V, 1.0, Fm, V));
       }
@@ -1308,7 +1426,13 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       int jdone = 0;
       for (int j = 0; j < m; ++j) {
         double* w = V + (int64_t)(j + 1) * nv;
-        NT_TRY(krylov_apply(g, U, V + (int64_t)j * nv, w, nullptr, o.sigma, cur_prec, o.simple_eps,
+        const double* vj = V + (int64_t)j * nv;
+        if (pre) {                             // z_j = M^-1 v_j, w = A z_j
+          double* zj = Z + (int64_t)j * nv;
+          NT_TRY(stokes_precond_apply(g, vj, zj, o.precond_sigma));
+          vj = zj;
+        }
+        NT_TRY(krylov_apply(g, nullptr, vj, w, nullptr, o.sigma, cur_prec, o.simple_eps,
                             200, 1.0, nullptr));
         double hn;
         NT_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn, cur_prec != FV_FP64));
@@ -1342,14 +1466,14 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       }
       NT_CUDA(cudaMemcpyAsync(g->kry_small, y.data(), jdone * sizeof(double), cudaMemcpyHostToDevice,
                               g->stream));
-      NT_TRY(vec_update(g, du, V, nv, jdone, g->kry_small, 1.0, cur_prec != FV_FP64));
+      NT_TRY(vec_update(g, du, pre ? Z : V, nv, jdone, g->kry_small, 1.0, cur_prec != FV_FP64));
       NT_CUDA(cudaStreamSynchronize(g->stream));
     }
     st.gmres_total += its;
     if (!converged && o.linear != FV_LIN_GMRES && its < o.gmres_max_it) {
       int mv = 0;
       double rn;
-      NT_TRY(bicgstab2(g, U, Fm, du, stop, o.gmres_max_it - its, cur_prec, o.sigma, o.simple_eps,
+      NT_TRY(bicgstab2(g, nullptr, Fm, du, stop, o.gmres_max_it - its, cur_prec, o.sigma, o.simple_eps,
                        &mv, &rn));
       st.bicgstab_total += mv;
     }
@@ -1388,8 +1512,9 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
   FV_TRY(ensure_krylov(g, gs_ff ? m + 3 : m + 1));
   {
     int w;                                     // forget statuses of earlier evaluations
-    FV_TRY(graph_take_status(g, &w));
+    FV_TRY(graph_take_status(g, &w, false));
   }
+  FV_TRY(set_base(g, U));                      // U converted once for every Krylov vector
   const int64_t nv = g->nvel;
   double* V = g->kry;
   float2* Vf = (float2*)g->kry;
@@ -1409,7 +1534,27 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
   else
     FV_TRY(vec_axpby(g, nv, 1.0 / std::sqrt(nrm), V, 0.0, nullptr, V));
 
-  std::vector<double> H((size_t)(m + 1) * m, 0.0), hcol(m + 2);
+  // The Arnoldi steps of a cycle run without host round trips: each
+  // Gram-Schmidt writes its coefficients and the new vector's norm into the
+  // FP64 Hessenberg H held in device memory, and the new basis vector is
+  // scaled by that norm on the device.  The host copies H once per cycle for
+  // the small dense work (Ritz values by Francis QR, Ritz estimates, exact
+  // shifts, the recombination matrix; fv_dense.cu) and sends the
+  // recombination matrix back.
+  if (!g->d_arn) {
+    const size_t bytes = (size_t)((kMaxVec + 1) * kMaxVec + 8) * sizeof(double);
+    cudaError_t e = cudaMalloc(&g->d_arn, bytes);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      g->d_arn = nullptr;
+      set_error("arnoldi_leading: device area allocation failed");
+      return FV_ENOMEM;
+    }
+  }
+  double* dH = (double*)g->d_arn;
+  double* dsc = dH + (kMaxVec + 1) * kMaxVec;   // 1 / norm of the new vector
+  FV_CUDA(cudaMemsetAsync(dH, 0, (size_t)(m + 1) * m * sizeof(double), g->stream));
+  std::vector<double> H((size_t)(m + 1) * m, 0.0);
   std::vector<double> Hm((size_t)m * m), Q((size_t)m * m), wr(m), wi(m);
   const int k_base = std::min(nev + (m - nev) / 2, m - 2);
   int k = 0, matvecs = 0;
@@ -1423,22 +1568,19 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
         xj = xs;
         w = ws;
       }
-      FV_TRY(krylov_apply(g, U, xj, w, nullptr, o.sigma, o.prec, o.simple_eps, 200, 1.0, nullptr));
+      FV_TRY(krylov_apply(g, nullptr, xj, w, nullptr, o.sigma, o.prec, o.simple_eps, 200, 1.0, nullptr));
       ++matvecs;
-      double hn;
-      if (gs_ff)
-        FV_TRY(cgs2_ffb(g, Vf, j + 1, w, hcol.data(), &hn));
-      else
-        FV_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn, false));
-      if (!(hn > 0) || !std::isfinite(hn)) { set_error("arnoldi_leading: breakdown"); return FV_ENAN; }
-      if (gs_ff)
-        FV_TRY(ffb_store(g, w, 1.0 / hn, Vf + (int64_t)(j + 1) * nv));
-      else
-        FV_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
-      H[(size_t)(j + 1) * m + j] = hn;
+      FV_TRY(cgs2_dev(g, gs_ff ? Vf : nullptr, V, j + 1, w, dH + j, m, dsc, false));
+      FV_TRY(store_scaled(g, w, dsc, gs_ff ? Vf + (int64_t)(j + 1) * nv : nullptr, w));
     }
     FV_TRY(check_products(g, o.prec));
+    FV_CUDA(cudaMemcpyAsync(H.data(), dH, (size_t)(m + 1) * m * sizeof(double), cudaMemcpyDeviceToHost,
+                            g->stream));
+    FV_CUDA(cudaStreamSynchronize(g->stream));
+    for (int j = k; j < m; ++j) {
+      const double hn = H[(size_t)(j + 1) * m + j];
+      if (!(hn > 0) || !std::isfinite(hn)) { set_error("arnoldi_leading: breakdown"); return FV_ENAN; }
+    }
     for (int i = 0; i < m; ++i)
       for (int j = 0; j < m; ++j) Hm[(size_t)i * m + j] = H[(size_t)i * m + j];
     if (!hess_eigenvalues(m, Hm.data(), wr.data(), wi.data())) {
@@ -1469,7 +1611,8 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
         for (int q = 0; q < nev && q < 64; ++q) stats->ritz_resid[q] = resid[q];
       }
       if (evec) {
-        // leading Ritz vector x = V y (complex), unit W-norm, phase fixed
+        // leading Ritz vector x = V y (complex), unit W-norm, phase: its
+        // largest-modulus entry real positive, found by a device argmax
         hess_eigvec(m, Hm.data(), wr[ord[0]], wi[ord[0]], yr.data(), yi.data());
         std::vector<double> C((size_t)m * 2);
         for (int i = 0; i < m; ++i) { C[2 * i] = yr[i]; C[2 * i + 1] = yi[i]; }
@@ -1483,17 +1626,21 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
         FV_TRY(dot_host(g, evec, evec, &a2));
         FV_TRY(dot_host(g, evec + nv, evec + nv, &b2));
         const double inv = 1.0 / std::sqrt(a2 + b2);
-        // phase: largest-modulus entry real positive
-        std::vector<double> hx(2 * nv);
-        FV_CUDA(cudaMemcpyAsync(hx.data(), evec, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
-        FV_CUDA(cudaStreamSynchronize(g->stream));
-        int64_t big = 0;
-        double bm = -1;
-        for (int64_t e = 0; e < nv; ++e) {
-          const double mm = hx[e] * hx[e] + hx[nv + e] * hx[nv + e];
-          if (mm > bm) { bm = mm; big = e; }
+        const int nb = (int)std::min<int64_t>(152 * 4, (nv + 255) / 256);
+        double* pv = (double*)g->d_part;
+        int64_t* pidx = (int64_t*)(pv + 1024);
+        double* big = pv + 2048;
+        {
+          LaunchScope ls_(g, FV_K_VECTOR);
+          k_absmax_c<<<nb, 256, 0, g->stream>>>(nv, evec, evec + nv, pv, pidx);
+          k_absmax_c_final<<<1, 32, 0, g->stream>>>(nb, pv, pidx, evec, evec + nv, big);
         }
-        const double pr = hx[big] / std::sqrt(bm), pi = -hx[nv + big] / std::sqrt(bm);
+        FV_CHECK_LAUNCH();
+        double hb[2];
+        FV_CUDA(cudaMemcpyAsync(hb, big, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+        FV_CUDA(cudaStreamSynchronize(g->stream));
+        const double bm = std::sqrt(hb[0] * hb[0] + hb[1] * hb[1]);
+        const double pr = hb[0] / bm, pi = -hb[1] / bm;
         // (a + i b)(pr + i pi) = (a pr - b pi) + i (a pi + b pr)
         const double Cph[4] = {pr * inv, pi * inv, -pi * inv, pr * inv};
         FV_CUDA(cudaMemcpyAsync(g->kry_small, Cph, 4 * sizeof(double), cudaMemcpyHostToDevice, g->stream));
@@ -1529,23 +1676,22 @@ fv_status arnoldi_leading(const fv_grid* gc, const double* U, const double* v0, 
     C[(size_t)m * (k + 1) + k] = fscale;
     FV_CUDA(cudaMemcpyAsync(g->kry_small, C.data(), C.size() * sizeof(double),
                             cudaMemcpyHostToDevice, g->stream));
-    // re-orthogonalise f against the kept vectors, normalise
-    double hn;
     if (gs_ff) {
       FV_TRY(ffb_combine<float2>(g, Vf, m + 1, g->kry_small, k + 1, Vf));
       FV_TRY(ffb_load(g, Vf + (int64_t)k * nv, ws));
-      FV_TRY(cgs2_ffb(g, Vf, k, ws, hcol.data(), &hn));
-      FV_TRY(ffb_store(g, ws, 1.0 / hn, Vf + (int64_t)k * nv));
     } else {
       FV_TRY(vec_combine(g, V, nv, m + 1, g->kry_small, k + 1, V, nv, false));
-      double* f = V + (int64_t)k * nv;
-      FV_TRY(cgs2(g, V, k, f, hcol.data(), &hn, false));
-      FV_TRY(vec_axpby(g, nv, 1.0 / hn, f, 0.0, nullptr, f));
     }
+    // the new H: the leading k x k block of the shifted Hm; H[k][k-1] = ||f||
+    // after f is re-orthogonalised against the kept vectors (on the device)
     std::fill(H.begin(), H.end(), 0.0);
     for (int i = 0; i < k; ++i)
       for (int j = 0; j < k; ++j) H[(size_t)i * m + j] = Hm[(size_t)i * m + j];
-    H[(size_t)k * m + (k - 1)] = hn;
+    FV_CUDA(cudaMemcpyAsync(dH, H.data(), (size_t)(m + 1) * m * sizeof(double), cudaMemcpyHostToDevice,
+                            g->stream));
+    double* f = gs_ff ? ws : V + (int64_t)k * nv;
+    FV_TRY(cgs2_dev(g, gs_ff ? Vf : nullptr, V, k, f, dH + (k - 1), m, dsc, true));
+    FV_TRY(store_scaled(g, f, dsc, gs_ff ? Vf + (int64_t)k * nv : nullptr, f));
   }
   set_error("arnoldi_leading: max_restarts reached");
   return FV_ENOCONV;

@@ -13,6 +13,7 @@
 #include "fv_internal.cuh"
 #include "fv_stencil_dev.cuh"
 #include "fv_tc5.cuh"
+#include "fv_jv.cuh"
 
 namespace fv {
 
@@ -161,35 +162,6 @@ __global__ void k_split_ff(const double* __restrict__ in, float2* __restrict__ o
     out[e] = to2(f64_split(__ldg(in + e)));
 }
 
-// J.v (Eq. 10) in float-float arithmetic: same stencil template as the
-// float32 / float64 kernels, instantiated with the float-float number type
-// (this file is compiled without FMA contraction, so every TwoSum and
-// TwoProd keeps its rounding)
-__global__ void __launch_bounds__(256) k_momentum_ff(Met<ffn> m, const float2* __restrict__ U,
-                                                     const float2* __restrict__ V,
-                                                     float2* __restrict__ out, ffn inv_re,
-                                                     ffn shift) {
-  const int plane_ = m.n[0] * m.n[1];
-  const int t_ = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t_ >= plane_) return;
-  const int i = t_ % m.n[0], j = t_ / m.n[0];
-  const int st[3] = {1, m.n[0], plane_};
-  const int nc = (int)m.ncell;
-  for (int kk = 0; kk < kCellKz; ++kk) {
-    const int k = blockIdx.y * kCellKz + kk;
-    if (k >= m.n[2]) return;
-    const int pos[3] = {i, j, k};
-    const int base = k * plane_ + t_;
-    ffn r0, r1, r2;
-    if (i > 0) r0 = stencil::momentum_face<ffn, 0, true, float2>(m, U, V, base, pos, st, inv_re, ffn(0), shift);
-    if (j > 0) r1 = stencil::momentum_face<ffn, 1, true, float2>(m, U, V, base, pos, st, inv_re, ffn(0), shift);
-    if (k > 0) r2 = stencil::momentum_face<ffn, 2, true, float2>(m, U, V, base, pos, st, inv_re, ffn(0), shift);
-    out[base] = make_float2(r0.hi, r0.lo);
-    out[nc + base] = make_float2(r1.hi, r1.lo);
-    out[2 * nc + base] = make_float2(r2.hi, r2.lo);
-  }
-}
-
 // D w of a float-float field, rounded to float32 (first pressure rhs of FV_FF)
 __global__ void __launch_bounds__(256) k_div_ff(MetFF m, const float2* __restrict__ w,
                                                 float* __restrict__ r) {
@@ -294,15 +266,50 @@ fv_status launch_split_ff(const fv_grid* g, const double* in, float2* out, int64
   return FV_OK;
 }
 
-fv_status launch_momentum_ff(const fv_grid* g, const float2* U, const float2* v, float2* out,
-                             double shift) {
-  const ff ir = f64_split(1.0 / g->re), sh = f64_split(shift);
+// float-float J.v (FV_FF): U from Ud (float64, split into g->Uff first,
+// which drops a registered base flow) or, when Ud is null, from the grid's
+// registered base flow g->Uff; x float64 split as its planes are staged;
+// float-float result (this file is compiled without FMA contraction, so
+// every TwoSum and TwoProd keeps its rounding)
+fv_status launch_jv_ff(const fv_grid* g, const double* Ud, const double* x, float2* out,
+                       double shift, const void* call) {
+  if (Ud) {
+    FV_TRY(launch_split_ff(g, Ud, g->Uff, g->nvel));
+    const_cast<fv_grid*>(g)->base_ptr = nullptr;
+  }
+  jv::Args<ffn, float2, float2> a;
+  a.m = g->met_fn;
+  a.Ur = g->Uff;
+  a.x = x;
+  a.out = out;
+  a.call = (const jv::CallPtrs*)call;
+  a.inv_re = ffn(f64_split(1.0 / g->re));
+  a.shift = ffn(f64_split(shift));
   {
     LaunchScope ls_(g, FV_K_MOMENTUM);
-    k_momentum_ff<<<cell_grid(g, 0), kCellThreads, 0, g->stream>>>(
-        g->met_fn, U, v, out, ffn(ir), ffn(sh));
+    FV_CUDA(jv::launch(a, g->stream));
   }
-  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_jv_ff_out64(const fv_grid* g, const double* Ud, const double* x, double* out,
+                             double shift) {
+  if (Ud) {
+    FV_TRY(launch_split_ff(g, Ud, g->Uff, g->nvel));
+    const_cast<fv_grid*>(g)->base_ptr = nullptr;
+  }
+  jv::Args<ffn, float2, double> a;
+  a.m = g->met_fn;
+  a.Ur = g->Uff;
+  a.x = x;
+  a.out = out;
+  a.call = nullptr;
+  a.inv_re = ffn(f64_split(1.0 / g->re));
+  a.shift = ffn(f64_split(shift));
+  {
+    LaunchScope ls_(g, FV_K_MOMENTUM);
+    FV_CUDA(jv::launch(a, g->stream));
+  }
   return FV_OK;
 }
 
@@ -312,6 +319,13 @@ fv_status launch_div_ff(const fv_grid* g, const float2* w, float* r32) {
     k_div_ff<<<cell_grid(g, 0), kCellThreads, 0, g->stream>>>(g->met_ff, w, r32);
   }
   FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status set_base(fv_grid* g, const double* U) {
+  FV_TRY(launch_round_f32(g, U, g->U32, g->nvel));
+  FV_TRY(launch_split_ff(g, U, g->Uff, g->nvel));
+  g->base_ptr = U;
   return FV_OK;
 }
 

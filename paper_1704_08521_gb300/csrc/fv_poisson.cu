@@ -7,7 +7,11 @@
 // register-tiled shared-memory kernel (64 x 64 outputs per block, 4 x 4 per
 // thread); the eigenvalue scaling is fused into the epilogue of the third
 // forward transform.  float32 in the mixed mode, float64 otherwise.
+#include <atomic>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "fv_ff.cuh"
@@ -289,7 +293,7 @@ fv_status run_left(const fv_grid* g, int axis, const T* M, const TI* in, TO* out
     {
       LaunchScope ls_(g, FV_K_TPF_YZ);
       k_gemm32<float, TI, TO, true, SCALE><<<grid, GT, 0, g->stream>>>(
-          M, 0, n, in, (int64_t)n * Q, Q, out, (int64_t)n * Q, Q, n, Q, n, g->tpf_f);
+          M, 0, n, in, (int64_t)n * Q, Q, out, (int64_t)n * Q, Q, n, Q, n, tp);
     }
     FV_CHECK_LAUNCH();
     return FV_OK;
@@ -331,8 +335,9 @@ __host__ __device__ __forceinline__ int up8(int n) { return (n + 7) & ~7; }
 // round-off), which keeps the transforms at float32-level accuracy (~22
 // significant bits).  One block owns a 128-row accumulator (rows padded to
 // 128); one thread issues the MMAs and commits them to an mbarrier that the
-// block waits on (with an iteration limit: on timeout the outputs become NaN,
-// which the SIMPLE loop reports).  The eigenbases come pre-split and
+// block waits on (with an iteration limit: on timeout the block sets the
+// grid's sticky fault word, which the SIMPLE loop reports as FV_ETIMEOUT, and
+// its outputs become NaN).  The eigenbases come pre-split and
 // pre-laid-out (TcMats) and are copied to shared memory with 16-byte
 // cp.async; field values are split by the threads that store them.
 
@@ -408,7 +413,8 @@ __global__ void __launch_bounds__(kUmmaThreads) k_slab_umma(const float* __restr
                                                             float* __restrict__ out,
                                                             const float* __restrict__ bx,
                                                             const float* __restrict__ ay, int nx, int ny,
-                                                            int Na, uint32_t tcols, int vec) {
+                                                            int Na, uint32_t tcols, int vec,
+                                                            unsigned* __restrict__ fault) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
@@ -507,6 +513,7 @@ __global__ void __launch_bounds__(kUmmaThreads) k_slab_umma(const float* __restr
   const bool ok2 = tc5::mbar_wait(&bar, 1, kMbarLimit);
   __syncwarp();
   tc5::fence_after_sync();
+  if (tid == 0 && !(ok1 && ok2)) atomicOr(fault, 1u);   // reported as FV_ETIMEOUT
   {
     float* outr = out + (size_t)k * nx * ny + (size_t)row * nx;
     const int half = ((Na >> 3) + 1) >> 1;
@@ -547,7 +554,8 @@ __global__ void __launch_bounds__(kUmmaThreads) k_col_umma(const float* __restri
                                                            float* __restrict__ out, TpfDev<float> tp,
                                                            const float* __restrict__ azi,
                                                            const float* __restrict__ aze, int N,
-                                                           uint32_t tcols, int vec) {
+                                                           uint32_t tcols, int vec,
+                                                           unsigned* __restrict__ fault) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
@@ -681,6 +689,7 @@ __global__ void __launch_bounds__(kUmmaThreads) k_col_umma(const float* __restri
   const bool ok2 = tc5::mbar_wait(&bar, 1, kMbarLimit);
   __syncwarp();
   tc5::fence_after_sync();
+  if (tid == 0 && !(ok1 && ok2)) atomicOr(fault, 1u);   // reported as FV_ETIMEOUT
   for (int c = c_begin; c < c_end; c += 8) {
     float v[8];
     tc5::ld8(trow + (uint32_t)c, v);
@@ -761,14 +770,15 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 
 // dir 0: forward (Einv) transforms, 1: inverse (E)
 fv_status launch_slab(const fv_grid* g, const float* in, float* out, int dir) {
+  // dir 0: forward x-y transforms, dir 1: inverse
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   const int N = g->tc.slab_n;
-  LaunchScope ls_(g, FV_K_TPF_X);
+  LaunchScope ls_(g, dir == 0 ? FV_K_TPF_X : FV_K_TPF_XINV);
   FV_CUDA(launch_pdl(k_slab_umma, dim3(nz, g->tc.slab_nsplit), dim3(kUmmaThreads),
                      slab_smem(nx, ny, N), g->stream, in, out, (const float*)g->tc.bx[dir],
                      (const float*)g->tc.ay[dir], nx, ny, N,
                      tmem_cols(up16(ny) > N ? up16(ny) : N),
-                     (nx % 4 == 0 && N % 4 == 0) ? 1 : 0));
+                     (nx % 4 == 0 && N % 4 == 0) ? 1 : 0, g->d_fault));
   return FV_OK;
 }
 
@@ -779,7 +789,7 @@ fv_status launch_col(const fv_grid* g, const float* in, float* out) {
   FV_CUDA(launch_pdl(k_col_umma, dim3((unsigned)((Q + N - 1) / N)), dim3(kUmmaThreads),
                      col_smem(g->n[2], N), g->stream, in, out, g->tpf_f,
                      (const float*)g->tc.az[0], (const float*)g->tc.az[1], N, tmem_cols(N),
-                     (Q % 4 == 0 && N % 4 == 0) ? 1 : 0));
+                     (Q % 4 == 0 && N % 4 == 0) ? 1 : 0, g->d_fault));
   return FV_OK;
 }
 
@@ -895,6 +905,12 @@ fv_status build_tc_mats(fv_grid* g) {
   return FV_OK;
 }
 
+// The unfused float32 tensor-product solve with the tables of tp (the
+// pressure operator's, or those of another separable operator)
+fv_status tpf_run_f32(const fv_grid* g, const TpfDev<float>& tp, const float* r, float* phi) {
+  return tpf_run<float, float, float>(g, tp, r, phi);
+}
+
 fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec) {
   if (prec == FV_MIXED) return tpf_run<float, double, float>(g, g->tpf_f, r, (float*)phi);
   return tpf_run<double, double, double>(g, g->tpf_d, r, (double*)phi);
@@ -912,7 +928,7 @@ fv_status tpf_one_transform_f32(const fv_grid* g, int axis) {
   float* b = (float*)g->tpf_buf[1];
   if (fused_ok(g)) {          // fused kernels: axis 0 = one slab kernel, else one column kernel
     FV_TRY(set_tc_attributes());
-    return axis == 0 ? launch_slab(g, a, b, 0) : launch_col(g, a, b);
+    return axis == 2 ? launch_col(g, a, b) : launch_slab(g, a, b, axis);
   }
   if (axis == 0) return run_right<float, float, float>(g, g->tpf_f.Einv[0], a, b);
   return run_left<float, float, float, false>(g, axis, g->tpf_f.Einv[axis], a, b, g->tpf_f);
@@ -936,8 +952,7 @@ extern "C" fv_status fv_pressure_solve(const fv_grid* g, const double* r, double
 // Allocation-free pressure-correction solve.
 //
 // Some callers cannot allocate device memory: code that runs inside a
-// memory pool it does not own, callers in the middle of a CUDA graph
-// capture (where cudaMalloc is not allowed), or embedded users whose
+// memory pool it does not own and may not grow, or embedded users whose
 // allocator is not reachable from this library.  For them
 // fv_pressure_solve_noalloc runs the float32 tensor-product solve with all
 // of its scratch (the per-axis eigenbases and the two transform buffers) in
@@ -947,6 +962,16 @@ extern "C" fv_status fv_pressure_solve(const fv_grid* g, const double* r, double
 // call in the process: its contents are overwritten by each call (nothing in
 // it needs to start at zero: the tables and both buffers are fully written
 // before they are read), and calls that overlap on the GPU race on it.
+//
+// The module that holds the array is loaded lazily (CUDA's default), so the
+// first call on a device, which looks up the array's device address with
+// cudaGetSymbolAddress, is the one that makes the driver reserve the array;
+// later calls reserve nothing.
+//
+// The host-side eigenbasis tables of an axis (n, map) are computed once and
+// kept for the life of the process (an immutable cache under a mutex), so
+// the asynchronous upload of a call always reads memory that outlives it and
+// later calls do not repeat the O(n^3) eigensolve.
 namespace fv {
 namespace {
 
@@ -958,19 +983,47 @@ constexpr int64_t kNaFloats = kNaTables + 2 * kNaMaxCells;
 static __device__ __align__(256) float g_na_scratch[kNaFloats];
 
 // device address of g_na_scratch per device, looked up once per device
-static float* g_na_ptr[64] = {nullptr};
+static std::atomic<float*> g_na_ptr[64];
 
 fv_status na_scratch_address(float** out) {
   int dev = 0;
   FV_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) { set_error("fv_pressure_solve_noalloc: device index out of range"); return FV_EINVAL; }
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    FV_CUDA(cudaGetSymbolAddress(&p, g_na_scratch));
-    g_na_ptr[dev] = (float*)p;
+  float* p = g_na_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    // two threads that race here both store the same address
+    void* q = nullptr;
+    FV_CUDA(cudaGetSymbolAddress(&q, g_na_scratch));
+    p = (float*)q;
+    g_na_ptr[dev].store(p, std::memory_order_release);
   }
-  *out = g_na_ptr[dev];
+  *out = p;
   return FV_OK;
+}
+
+// float32 [E | Einv | lam] of one axis, built once per (n, map)
+struct NaAxis {
+  std::vector<float> tab;
+  int null_index = 0;
+};
+
+const NaAxis* na_axis_tables(int n, int map) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, std::unique_ptr<NaAxis>> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({n, map});
+  if (it != cache.end()) return it->second.get();
+  AxisBasis B;
+  if (!host_axis_tables(n, map, B)) return nullptr;
+  auto a = std::make_unique<NaAxis>();
+  a->tab.reserve(2 * (size_t)n * n + n);
+  for (double v : B.E) a->tab.push_back((float)v);
+  for (double v : B.Einv) a->tab.push_back((float)v);
+  for (double v : B.lam) a->tab.push_back((float)v);
+  a->null_index = B.null_index;
+  const NaAxis* r = a.get();
+  cache.emplace(std::make_pair(n, map), std::move(a));
+  return r;
 }
 
 template <typename TI, typename TO>
@@ -1016,27 +1069,20 @@ extern "C" fv_status fv_pressure_solve_noalloc(int nx, int ny, int nz, int map, 
   FV_TRY(na_scratch_address(&base));
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // tables: E, Einv, lam per axis, packed at the start of the scratch array
-  std::vector<float> tab;
   TpfDev<float> tp;
-  size_t off[3][3];
+  float* dst = base;
   for (int d = 0; d < 3; ++d) {
-    AxisBasis B;
-    if (!host_axis_tables(n[d], map, B)) { set_error("fv_pressure_solve_noalloc: eigensolver failed"); return FV_ECUDA; }
-    off[d][0] = tab.size();
-    for (double v : B.E) tab.push_back((float)v);
-    off[d][1] = tab.size();
-    for (double v : B.Einv) tab.push_back((float)v);
-    off[d][2] = tab.size();
-    for (double v : B.lam) tab.push_back((float)v);
+    const NaAxis* A = na_axis_tables(n[d], map);
+    if (!A) { set_error("fv_pressure_solve_noalloc: eigensolver failed"); return FV_ECUDA; }
+    const size_t nn = (size_t)n[d] * n[d];
     tp.n[d] = n[d];
-    tp.null_index[d] = B.null_index;
+    tp.null_index[d] = A->null_index;
+    tp.E[d] = dst;
+    tp.Einv[d] = dst + nn;
+    tp.lam[d] = dst + 2 * nn;
+    FV_CUDA(cudaMemcpyAsync(dst, A->tab.data(), A->tab.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    dst += A->tab.size();
   }
-  for (int d = 0; d < 3; ++d) {
-    tp.E[d] = base + off[d][0];
-    tp.Einv[d] = base + off[d][1];
-    tp.lam[d] = base + off[d][2];
-  }
-  FV_CUDA(cudaMemcpyAsync(base, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   float* a = base + kNaTables;
   float* b = a + kNaMaxCells;
   const int64_t rows = (int64_t)ny * nz, qxy = (int64_t)nx * ny;

@@ -12,6 +12,7 @@
 #include "fv_ff.cuh"
 #include "fv_internal.cuh"
 #include "fv_stencil_dev.cuh"
+#include "fv_jv.cuh"
 
 namespace fv {
 
@@ -203,37 +204,66 @@ inline int block_x(const fv_grid*) { return kCellThreads; }
 
 fv_status launch_momentum_jac(const fv_grid* g, const double* U, const double* v, double* out,
                               int prec, double shift) {
-  const int bx = block_x(g);
-  if (prec == FV_MIXED) {
-    // float32 operands (rounded once, integer conversion), float32 J.v,
-    // exact widening of the result
-    FV_TRY(launch_round_f32(g, U, g->U32, g->nvel));
-    FV_TRY(launch_round_f32(g, v, g->x32, g->nvel));
-    {
-      LaunchScope ls_(g, FV_K_MOMENTUM);
-      k_momentum<float, true, float, double><<<cell_grid(g, bx), bx, 0, g->stream>>>(
-          g->met_f, g->U32, g->x32, nullptr, out, float(1.0 / g->re), 0.f, 0.f, float(shift));
-    }
-  } else {
-    {
-      LaunchScope ls_(g, FV_K_MOMENTUM);
-      k_momentum<double, true, double, double><<<cell_grid(g, bx), bx, 0, g->stream>>>(
-          g->met_d, U, v, nullptr, out, 1.0 / g->re, 0.0, 0.0, shift);
-    }
+  if (prec == FV_MIXED) return launch_jv_f32_out64(g, U, v, out, shift);
+  jv::Args<double, double, double> a;
+  a.m = g->met_d;
+  a.Ur = U;
+  a.x = v;
+  a.out = out;
+  a.call = nullptr;
+  a.inv_re = 1.0 / g->re;
+  a.shift = shift;
+  {
+    LaunchScope ls_(g, FV_K_MOMENTUM);
+    FV_CUDA(jv::launch(a, g->stream));
   }
-  FV_CHECK_LAUNCH();
   return FV_OK;
 }
 
-fv_status launch_momentum_f32(const fv_grid* g, const float* U32, const float* v32, float* out,
-                              double shift) {
-  const int bx = block_x(g);
+// float32 J.v of the mixed form: U from Ud (float64, rounded into g->U32
+// first, which drops a registered base flow) or, when Ud is null, from the
+// grid's registered base flow g->U32; x float64 rounded as its planes are
+// staged; float32 result.  call: graph launches read x from the evaluation's
+// device call block (whose U the graph has already rounded into g->U32).
+fv_status launch_jv_f32(const fv_grid* g, const double* Ud, const double* x, float* out,
+                        double shift, const void* call) {
+  if (Ud) {
+    FV_TRY(launch_round_f32(g, Ud, g->U32, g->nvel));
+    const_cast<fv_grid*>(g)->base_ptr = nullptr;
+  }
+  jv::Args<float, float, float> a;
+  a.m = g->met_f;
+  a.Ur = g->U32;
+  a.x = x;
+  a.out = out;
+  a.call = (const jv::CallPtrs*)call;
+  a.inv_re = float(1.0 / g->re);
+  a.shift = float(shift);
   {
     LaunchScope ls_(g, FV_K_MOMENTUM);
-    k_momentum<float, true, float, float><<<cell_grid(g, bx), bx, 0, g->stream>>>(
-        g->met_f, U32, v32, nullptr, out, float(1.0 / g->re), 0.f, 0.f, float(shift));
+    FV_CUDA(jv::launch(a, g->stream));
   }
-  FV_CHECK_LAUNCH();
+  return FV_OK;
+}
+
+fv_status launch_jv_f32_out64(const fv_grid* g, const double* Ud, const double* x, double* out,
+                              double shift) {
+  if (Ud) {
+    FV_TRY(launch_round_f32(g, Ud, g->U32, g->nvel));
+    const_cast<fv_grid*>(g)->base_ptr = nullptr;
+  }
+  jv::Args<float, float, double> a;
+  a.m = g->met_f;
+  a.Ur = g->U32;
+  a.x = x;
+  a.out = out;
+  a.call = nullptr;
+  a.inv_re = float(1.0 / g->re);
+  a.shift = float(shift);
+  {
+    LaunchScope ls_(g, FV_K_MOMENTUM);
+    FV_CUDA(jv::launch(a, g->stream));
+  }
   return FV_OK;
 }
 

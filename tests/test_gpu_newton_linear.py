@@ -88,3 +88,40 @@ def test_bad_linear_option(fv):
     P = torch.zeros(g.n_cell, dtype=torch.float64, device="cuda")
     with pytest.raises(fv.FvError):
         fv.newton_steady(g, U, P, linear=3)
+
+
+@pytest.mark.parametrize("prec", ["ff", "mixed"])
+def test_preconditioned_newton_same_steady_state(fv, prec):
+    """Newton with the Stokes-type right preconditioner (flexible GMRES):
+    the 16^3 continuation Re 200 -> 1000 from rest reaches the stored oracle
+    steady state to the same 1e-9, with fewer operator products than the
+    unpreconditioned GMRES(30) Newton (the correction does not depend on how
+    the linear system is solved)."""
+    gold = np.load(GOLD)
+    res = {}
+    for pre in (0, 1):
+        g = fv.Grid(16, 16, 16, "cosine", alpha=0.0, re=200.0)
+        U = torch.zeros(g.n_vel, dtype=torch.float64, device="cuda")
+        P = torch.zeros(g.n_cell, dtype=torch.float64, device="cuda")
+        tot = 0
+        for re in (200.0, 400.0, 600.0, 800.0, 1000.0):
+            g.set_re(re)
+            st = fv.newton_steady(g, U, P, tol=1e-10, prec=prec, linear="gmres", gmres_m=30,
+                                  precond=pre)
+            tot += st["gmres_total"]
+        torch.cuda.synchronize()
+        ref = gold["U"]
+        assert np.abs(U.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-9, pre
+        res[pre] = tot
+    print(f"\n16^3 continuation, {prec}: GMRES(30) products {res[0]}, preconditioned {res[1]}")
+    assert res[1] < res[0] / 2
+
+
+def test_bad_precond_option(fv):
+    g = fv.Grid(6, 6, 6, "cosine", re=100.0)
+    U = torch.zeros(g.n_vel, dtype=torch.float64, device="cuda")
+    P = torch.zeros(g.n_cell, dtype=torch.float64, device="cuda")
+    with pytest.raises(fv.FvError):
+        fv.newton_steady(g, U, P, precond=2)
+    with pytest.raises(fv.FvError):
+        fv.newton_steady(g, U, P, precond=1, precond_sigma=-1.0)

@@ -297,3 +297,22 @@ def test_nan_in_operator_is_reported(fv, prec):
     U2 = dev(synth.vortex_base_flow((n, n, n), "cosine", 0.0))
     lam, _ = fv.arnoldi_leading(g, U2, v0, m=20, nev=2, prec=prec, tol=1e-6)
     assert np.isfinite(np.array(lam)).all()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
+def test_registered_base_flow(fv, prec):
+    """fv_grid_set_base: evaluations with U = NULL use the registered base
+    flow and give the same vector as passing U (the same rounding / split of
+    U, made once instead of per evaluation)."""
+    g, G, shape, U, v = setup(fv, 14, 13, 15, "cosine")
+    tU, tv = dev(U), dev(v)
+    a = torch.empty(g.n_vel, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    fv.simple_krylov_solve(g, tU, tv, a, None, eps=1e-10, prec=prec, sigma=10.0)
+    g.set_base(tU)
+    fv.simple_krylov_solve(g, None, tv, b, None, eps=1e-10, prec=prec, sigma=10.0)
+    assert np.array_equal(host(a), host(b))
+    # no registered base on a fresh grid: U = NULL is refused
+    g2 = fv.Grid(15, 13, 14, "cosine", alpha=0.3, re=700.0)
+    with pytest.raises(fv.FvError):
+        fv.simple_krylov_solve(g2, None, tv, b, None, eps=1e-10, prec=prec)

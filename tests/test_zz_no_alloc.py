@@ -1,10 +1,12 @@
 """The allocation-free pressure solve (fv_pressure_solve_noalloc) against the
 grid-based entry point fv_pressure_solve in the same float32 arithmetic.
 
-It exists for callers that cannot allocate device memory (inside a foreign
-memory pool, during graph capture, without an allocator); its scratch lives
-in a fixed device array of the library.  This file is collected last so a
-failure here never hides the other tests; it passes alone and after them."""
+It exists for callers that cannot allocate device memory (inside a memory
+pool they do not own, or without an allocator); its scratch lives in a fixed
+device array of the library.  Besides matching the grid solve on two calls
+in a row, a call after the first one on the device must leave the device's
+free memory unchanged.  This file is collected last so a failure here never
+hides the other tests; it passes alone and after them."""
 import ctypes
 
 import numpy as np
@@ -48,6 +50,17 @@ def test_noalloc_matches_grid_solve_twice(fv, shape, kind):
         a, b = out.cpu().numpy(), ref.cpu().numpy()
         assert np.all(np.isfinite(a))
         assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max(), call
+    # once the first call on the device has reserved the array, a call takes
+    # no device memory: the driver's free-memory figure does not move
+    r = torch.tensor(_rhs(shape, 5), dtype=torch.float64, device="cuda")
+    out = torch.empty_like(r)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    st = fv.lib.fv_pressure_solve_noalloc(nx, ny, nz, fv.MAPS[kind], ctypes.c_void_p(r.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
+    torch.cuda.synchronize()
+    assert st == 0
+    assert torch.cuda.mem_get_info()[0] == free0
     g.close()
 
 

@@ -116,9 +116,11 @@ typedef struct {
                         Stokes-type right preconditioner M^-1 = P (s - Lap/Re)^-1
                         (vector Laplacian of the momentum equations, s =
                         precond_sigma, then the projection onto divergence-free
-                        fields) with flexible GMRES(m) (no BiCGstab(2)
-                        hand-off).  Same corrections; far fewer operator
-                        products on strongly stretched grids              [0] */
+                        fields) with flexible GMRES(m) and, after its
+                        saturation (linear = FV_LIN_GMRES_BICGSTAB), the
+                        right-preconditioned BiCGstab(2).  Same corrections;
+                        far fewer operator products on strongly stretched
+                        grids                                              [0] */
   double precond_sigma; /* s >= 0 of the preconditioner                    [0] */
 } fv_newton_opts;
 
@@ -243,6 +245,7 @@ typedef struct {
   int prec;           /* fv_prec of the Krylov vectors              [FV_FP64 = 0] */
   double newton_tol;  /* ||F||_inf of each steady state                  [1e-10] */
   double arnoldi_tol; /* Ritz tolerance                                  [1e-10] */
+  int precond;        /* fv_newton_opts.precond of the steady states          [0] */
 } fv_critical_opts;
 
 typedef struct {
@@ -355,6 +358,24 @@ fv_status fv_unet_train_step(fv_unet* u, const fv_grid* g, const double* r, cons
 fv_status simple_krylov_solve_guess(const fv_grid* g, fv_unet* u, const double* U,
                                     const double* v_in, double* v_out, double* p_out,
                                     const fv_simple_opts* opts, fv_simple_stats* stats);
+
+/* Section 4, Eqs. 11-17: the divergence-free projection of the velocity
+ * v[n_vel] (float64, device) onto a set of coordinate planes and its vector
+ * potential.  plane 0: the (x, z) planes -> v_1 = (u_1, 0, w_1) and
+ * Psi^(y); 1: the (y, z) planes -> v_2 = (0, v_2, w_2) and Psi^(x); 2: the
+ * (x, y) planes -> v_3 = (u_3, v_3, 0) and Psi^(z).  vp[n_vel] (device)
+ * receives the projection: the two in-plane components of v minus the
+ * gradient of phi, (L_a + L_c) phi = (in-plane divergence of v) solved
+ * exactly in every plane (Neumann walls), so that the in-plane divergence
+ * (Eqs. 12-14) vanishes to round-off; the normal component is zero.
+ * psi (device, optional) receives the potential on the corners of the
+ * planes' cells: a [k][j][i] array with n + 1 entries along the two in-plane
+ * axes and n along the normal one (e.g. (nz+1) x ny x (nx+1) for plane 0),
+ * zero on the walls, with v_1 = rot(0, Psi, 0), v_2 = rot(Psi, 0, 0),
+ * v_3 = rot(0, 0, Psi).  Wall entries of v are ignored.  v and vp may not
+ * alias.  float64 throughout. */
+fv_status fv_plane_projection(const fv_grid* g, const double* v, int plane, double* vp,
+                              double* psi);
 
 /* W-weighted inner product <a, b> = sum over velocity faces of the momentum
  * control-volume size times a b (wall faces excluded).  Result to host. */

@@ -195,7 +195,7 @@ def arnoldi_leading(g, U, v0, m=30, nev=5, evec=None, tol=1e-10, max_restarts=50
 class fv_critical_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("m", ctypes.c_int),
                 ("nev", ctypes.c_int), ("prec", ctypes.c_int), ("newton_tol", ctypes.c_double),
-                ("arnoldi_tol", ctypes.c_double)]
+                ("arnoldi_tol", ctypes.c_double), ("precond", ctypes.c_int)]
 
 
 class fv_critical_stats(ctypes.Structure):
@@ -204,9 +204,10 @@ class fv_critical_stats(ctypes.Structure):
 
 
 def fv_critical_re(g, U, P, v0, re0, re1, rtol=1e-8, max_iter=30, m=30, nev=4, prec="fp64",
-                   newton_tol=1e-10, arnoldi_tol=1e-10):
+                   newton_tol=1e-10, arnoldi_tol=1e-10, precond=0):
     """Secant search of Re_cr (Section 3); returns (re_cr, omega_cr, history)."""
-    o = fv_critical_opts(rtol, max_iter, m, nev, PRECS.get(prec, prec), newton_tol, arnoldi_tol)
+    o = fv_critical_opts(rtol, max_iter, m, nev, PRECS.get(prec, prec), newton_tol, arnoldi_tol,
+                         int(precond))
     s = fv_critical_stats()
     rc, om = ctypes.c_double(), ctypes.c_double()
     check(lib.fv_critical_re(g.handle, _f64(U, g.n_vel, "U"), _f64(P, g.n_cell, "P"),
@@ -215,6 +216,25 @@ def fv_critical_re(g, U, P, v0, re0, re1, rtol=1e-8, max_iter=30, m=30, nev=4, p
           "fv_critical_re")
     k = min(s.evaluations, 64)
     return rc.value, om.value, [(s.re_hist[i], s.sigma_hist[i], s.omega_hist[i]) for i in range(k)]
+
+
+PLANES = {"xz": 0, "yz": 1, "xy": 2}
+
+
+def fv_plane_projection(g, v, plane, vp, psi=None):
+    """Divergence-free projection of v onto the coordinate planes `plane`
+    ('xz', 'yz', 'xy') and its vector potential (Section 4, Eqs. 11-17)."""
+    nz, ny, nx = g.shape
+    pl = PLANES.get(plane, plane)
+    if psi is not None:
+        dims = [nx, ny, nz]
+        a, c = {0: (0, 2), 1: (1, 2), 2: (0, 1)}[pl]
+        dims[a] += 1
+        dims[c] += 1
+        npsi = dims[0] * dims[1] * dims[2]
+    check(lib.fv_plane_projection(g.handle, _f64(v, g.n_vel, "v"), pl, _f64(vp, g.n_vel, "vp"),
+                                  None if psi is None else _f64(psi, npsi, "psi")),
+          "fv_plane_projection")
 
 
 def fv_dot_w(g, a, b):

@@ -42,6 +42,7 @@ _SIGS = {
     "newton_steady": (_I, [_P, _P, _P, _P, _P]),
     "arnoldi_leading": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P]),
     "fv_dot_w": (_I, [_P, _P, _P, _P]),
+    "fv_plane_projection": (_I, [_P, _P, _I, _P, _P]),
     "ns_divergence": (_I, [_P, _P, _P]),
     "fv_unet_create": (_I, [ctypes.c_uint64, _P, ctypes.POINTER(_P)]),
     "fv_unet_destroy": (None, [_P]),

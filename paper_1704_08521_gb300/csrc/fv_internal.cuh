@@ -288,6 +288,9 @@ void destroy_graph_cache(GraphCache& c);
 // tensor-product pressure solve: phi = (D G)^+ r ; phi is float or double
 fv_status tpf_solve(const fv_grid* g, const double* r, void* phi, int prec);
 fv_status tpf_solve_f32(const fv_grid* g, const float* r, float* phi);
+// one float64 1-D transform along `axis` with the matrix M (n x n, row-major)
+fv_status transform_axis_f64(const fv_grid* g, int axis, const double* M, const double* in,
+                             double* out);
 // the unfused float32 transforms with the tables and eigenvalues of tp
 // (scaling by 1 / (lam_z + lam_y + lam_x); null_index -1: no null mode)
 fv_status tpf_run_f32(const fv_grid* g, const TpfDev<float>& tp, const float* r, float* phi);

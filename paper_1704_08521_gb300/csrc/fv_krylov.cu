@@ -1094,26 +1094,44 @@ static fv_status maxabs_host(const fv_grid* g, int64_t n, const double* x, doubl
 // product, from x (in/out), shadow residual = the initial residual; the
 // BiCGstab(l) recurrences written out for l = 2.  Section 3 runs it from the
 // last approximation of a saturated GMRES(m).  Uses Krylov columns 0..7 of
-// g->kry as r~, r_0..r_2, u_0..u_2 and the iterate of smallest residual.
+// g->kry as r~, r_0..r_2, u_0..u_2 and the iterate of smallest residual
+// (0..9 with a preconditioner: the preconditioned iterate y and M^-1 v).
 // Stops when the recursive residual W-norm is <= stop, after max_mv
 // products, on a zero BiCG / MR denominator, or when the residual turns
 // non-finite or grows 1e6-fold over the smallest seen; x is then the
 // iterate of smallest recursive residual.  *mv: products done.
+// pre: right preconditioning by the Stokes-type M^-1 (precond_sigma psig):
+// the recurrences run on A M^-1 from y = 0 and x becomes x_0 + M^-1 y_best
+// at the end (one more preconditioner application, no product).
 static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double* x, double stop,
-                           int max_mv, int prec, double sigma, double eps, int* mv,
-                           double* rnorm_out) {
+                           int max_mv, int prec, double sigma, double eps, bool pre, double psig,
+                           int* mv, double* rnorm_out) {
   const int64_t nv = g->nvel;
   double* rt = g->kry;
   double* r[3] = {g->kry + nv, g->kry + 2 * nv, g->kry + 3 * nv};
   double* u[3] = {g->kry + 4 * nv, g->kry + 5 * nv, g->kry + 6 * nv};
   double* xbest = g->kry + 7 * nv;
-  auto apply = [&](const double* in, double* out) {
+  double* yit = g->kry + 8 * nv;             // preconditioned iterate
+  double* tz = g->kry + 9 * nv;              // M^-1 of the vector being applied
+  auto plain = [&](const double* in, double* out) {
     ++*mv;
     return krylov_apply(g, U, in, out, nullptr, sigma, prec, eps, 200, 1.0, nullptr);
   };
+  auto apply = [&](const double* in, double* out) -> fv_status {
+    if (pre) {
+      FV_TRY(stokes_precond_apply(g, in, tz, psig));
+      in = tz;
+    }
+    return plain(in, out);
+  };
   *mv = 0;
-  FV_TRY(apply(x, r[0]));
+  FV_TRY(plain(x, r[0]));
   FV_TRY(vec_axpby(g, nv, -1.0, r[0], 1.0, b, r[0]));
+  double* const x0 = x;
+  if (pre) {                                 // iterate on y, x = x_0 + M^-1 y
+    FV_CUDA(cudaMemsetAsync(yit, 0, nv * sizeof(double), g->stream));
+    x = yit;
+  }
   FV_CUDA(cudaMemcpyAsync(rt, r[0], nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
   FV_CUDA(cudaMemsetAsync(u[0], 0, nv * sizeof(double), g->stream));
   double rho0 = 1.0, alpha = 0.0, omega = 1.0, rr, rho_next;
@@ -1126,7 +1144,12 @@ static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double*
   FV_CUDA(cudaMemcpyAsync(xbest, x, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
   auto finish = [&]() -> fv_status {        // hand back the best iterate
     FV_TRY(check_products(g, prec));
-    FV_CUDA(cudaMemcpyAsync(x, xbest, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    if (pre) {
+      FV_TRY(stokes_precond_apply(g, xbest, tz, psig));
+      FV_TRY(vec_axpby(g, nv, 1.0, x0, 1.0, tz, x0));
+    } else {
+      FV_CUDA(cudaMemcpyAsync(x, xbest, nv * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    }
     *rnorm_out = best;
     return FV_OK;
   };
@@ -1318,10 +1341,9 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     set_error("newton_steady: bad option (precond 0 or 1, precond_sigma >= 0)");
     return FV_EINVAL;
   }
-  const bool pre = o.precond == 1;
-  if (pre) o.linear = FV_LIN_GMRES;            // flexible GMRES(m) with the stored M^-1 v_j
+  const bool pre = o.precond == 1;            // flexible GMRES(m) with the stored M^-1 v_j
   const int m = o.gmres_m;
-  FV_TRY(ensure_krylov(g, pre ? 2 * m + 1 : std::max(m + 1, 8)));
+  FV_TRY(ensure_krylov(g, pre ? std::max(2 * m + 1, 10) : std::max(m + 1, 8)));
   {
     int w;                                     // forget statuses of earlier evaluations
     FV_TRY(graph_take_status(g, &w, false));
@@ -1474,7 +1496,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       int mv = 0;
       double rn;
       NT_TRY(bicgstab2(g, nullptr, Fm, du, stop, o.gmres_max_it - its, cur_prec, o.sigma, o.simple_eps,
-                       &mv, &rn));
+                       pre, o.precond_sigma, &mv, &rn));
       st.bicgstab_total += mv;
     }
     NT_TRY(vec_axpby(g, nv, 1.0, U, -1.0, du, U));
@@ -1718,6 +1740,7 @@ fv_status fv_critical_re(fv_grid* g, double* U, double* P, const double* v0, dou
   fv_newton_opts no = {};
   no.tol = o.newton_tol;
   no.prec = o.prec;
+  no.precond = o.precond;
   fv_arnoldi_opts ao = {};
   ao.tol = o.arnoldi_tol;
   ao.prec = o.prec;

@@ -905,6 +905,14 @@ fv_status build_tc_mats(fv_grid* g) {
   return FV_OK;
 }
 
+// One float64 1-D transform out = M applied along `axis` (0 x, 1 y, 2 z) of
+// the nz x ny x nx array `in` (the unfused kernels of the pressure solve)
+fv_status transform_axis_f64(const fv_grid* g, int axis, const double* M, const double* in,
+                             double* out) {
+  if (axis == 0) return run_right<double, double, double>(g, M, in, out);
+  return run_left<double, double, double, false>(g, axis, M, in, out, g->tpf_d);
+}
+
 // The unfused float32 tensor-product solve with the tables of tp (the
 // pressure operator's, or those of another separable operator)
 fv_status tpf_run_f32(const fv_grid* g, const TpfDev<float>& tp, const float* r, float* phi) {

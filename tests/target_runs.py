@@ -41,6 +41,7 @@ def main():
     ap.add_argument("--path", default="300,600,900,1200,1500,1800,1900")
     ap.add_argument("--eig-re", default="1900")
     ap.add_argument("--secant", default="", help="re0,re1 of a critical-Re secant search")
+    ap.add_argument("--secant-rtol", type=float, default=1e-6)
     ap.add_argument("--m", type=int, default=60)
     ap.add_argument("--nev", type=int, default=10)
     ap.add_argument("--prec", default="ff")
@@ -48,6 +49,12 @@ def main():
     ap.add_argument("--arnoldi-tol", type=float, default=1e-8)
     ap.add_argument("--max-restarts", type=int, default=20000)
     ap.add_argument("--precond", type=int, default=1)
+    ap.add_argument("--linear", default="gmres+bicgstab")
+    ap.add_argument("--gmres-m", type=int, default=100)
+    ap.add_argument("--gmres-rtol", type=float, default=1e-8)
+    ap.add_argument("--gmres-sat", type=float, default=0.5)
+    ap.add_argument("--load", default="", help=".npy velocity to start the continuation from")
+    ap.add_argument("--save", default="", help="write the last converged velocity here (.npy)")
     ap.add_argument("--verify", type=int, default=1)
     ap.add_argument("--out", default="target_run.json")
     a = ap.parse_args()
@@ -61,10 +68,13 @@ def main():
     path = [float(x) for x in a.path.split(",") if x]
     eig_re = [float(x) for x in a.eig_re.split(",") if x]
     res = {"n": n, "map": a.map, "alpha_deg": a.alpha, "prec": a.prec, "precond": a.precond,
+           "linear": a.linear, "gmres_m": a.gmres_m, "gmres_rtol": a.gmres_rtol, "load": a.load,
            "newton": [], "arnoldi": [], "critical": None, "verify": {}}
     dev = torch.device("cuda")
     g = fv.Grid(n, n, n, a.map, alpha=alpha, re=path[0])
     U = torch.zeros(g.n_vel, dtype=torch.float64, device=dev)
+    if a.load:
+        U.copy_(torch.from_numpy(np.load(a.load)))
     P = torch.zeros(g.n_cell, dtype=torch.float64, device=dev)
     v0 = torch.tensor(synth.gaussian_velocity((n, n, n), 1), device=dev)
     evec = torch.empty(2 * g.n_vel, dtype=torch.float64, device=dev)
@@ -77,16 +87,21 @@ def main():
     for re in path:
         g.set_re(re)
         t0 = sync_time()
+        U_prev = U.clone()
         st = fv.newton_steady(g, U, P, tol=a.newton_tol, prec=a.prec, precond=a.precond,
-                              linear="gmres" if a.precond else "gmres+bicgstab", gmres_m=100,
-                              gmres_max_it=20000, gmres_rtol=1e-8, max_newton=30, raise_on_fail=False)
+                              linear=a.linear, gmres_m=a.gmres_m, gmres_sat=a.gmres_sat,
+                              gmres_max_it=20000, gmres_rtol=a.gmres_rtol, max_newton=30,
+                              raise_on_fail=False)
         t1 = sync_time()
         rec = {"re": re, "s": t1 - t0, "status": st["status"], "steps": st["iterations"],
                "products": st["gmres_total"] + st["bicgstab_total"], "res": st["res_hist"]}
         res["newton"].append(rec)
         print(json.dumps(rec), flush=True)
         if st["status"] != 0:
+            U.copy_(U_prev)
             break
+        if a.save:
+            np.save(a.save, U.cpu().numpy())
         if re in eig_re:
             states[re] = U.clone()
             t0 = sync_time()
@@ -107,9 +122,9 @@ def main():
         r0, r1 = [float(x) for x in a.secant.split(",")]
         t0 = sync_time()
         try:
-            rc, om, hist = fv.fv_critical_re(g, U, P, v0, r0, r1, rtol=1e-8, m=a.m, nev=a.nev,
-                                             prec=a.prec, newton_tol=a.newton_tol,
-                                             arnoldi_tol=a.arnoldi_tol)
+            rc, om, hist = fv.fv_critical_re(g, U, P, v0, r0, r1, rtol=a.secant_rtol, m=a.m,
+                                             nev=a.nev, prec=a.prec, newton_tol=a.newton_tol,
+                                             arnoldi_tol=a.arnoldi_tol, precond=a.precond)
             res["critical"] = {"re_cr": rc, "omega_cr": om, "hist": hist}
         except fv.FvError as e:
             res["critical"] = {"error": str(e)}

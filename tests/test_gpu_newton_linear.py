@@ -117,6 +117,31 @@ def test_preconditioned_newton_same_steady_state(fv, prec):
     assert res[1] < res[0] / 2
 
 
+@pytest.mark.parametrize("linear", ["bicgstab", "gmres+bicgstab"])
+def test_preconditioned_bicgstab_same_steady_state(fv, linear):
+    """The right-preconditioned BiCGstab(2) (alone, and as the hand-off
+    after a saturated flexible GMRES(10)) reaches the stored oracle steady
+    state of the 16^3 continuation Re 200 -> 1000 to 1e-9."""
+    gold = np.load(GOLD)
+    g = fv.Grid(16, 16, 16, "cosine", alpha=0.0, re=200.0)
+    U = torch.zeros(g.n_vel, dtype=torch.float64, device="cuda")
+    P = torch.zeros(g.n_cell, dtype=torch.float64, device="cuda")
+    tot = [0, 0]
+    for re in (200.0, 400.0, 600.0, 800.0, 1000.0):
+        g.set_re(re)
+        st = fv.newton_steady(g, U, P, tol=1e-10, prec="ff", linear=linear, gmres_m=10,
+                              gmres_sat=0.9, precond=1)
+        tot[0] += st["gmres_total"]
+        tot[1] += st["bicgstab_total"]
+    torch.cuda.synchronize()
+    ref = gold["U"]
+    assert np.abs(U.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-9
+    assert tot[1] > 0
+    if linear == "bicgstab":
+        assert tot[0] == 0
+    print(f"\n16^3 continuation, preconditioned {linear}: GMRES {tot[0]}, BiCGstab(2) {tot[1]}")
+
+
 def test_bad_precond_option(fv):
     g = fv.Grid(6, 6, 6, "cosine", re=100.0)
     U = torch.zeros(g.n_vel, dtype=torch.float64, device="cuda")

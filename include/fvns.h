@@ -385,6 +385,38 @@ fv_status fv_dot_w(const fv_grid* g, const double* a, const double* b, double* o
  * (Neumann) by the tensor-product factorisation; prec as above. */
 fv_status fv_pressure_solve(const fv_grid* g, const double* r, double* phi, int prec);
 
+/* Section 3 step 1 by multigrid: phi[n_cell] (device, float64) = the
+ * solution of D G phi = r[n_cell] (device, float64) with Neumann walls, of
+ * zero volume-weighted mean -- the same phi as fv_pressure_solve.  Conjugate
+ * gradients in float64 on the symmetric form -V D G phi = -V r (r first made
+ * compatible with the null space: r - sum(V r)/sum(V)), preconditioned by
+ * one float32 V-cycle per iteration: full coarsening while an axis has more
+ * than 4 cells, alternating-direction damped line-Jacobi smoothing (one
+ * tridiagonal solve per grid line), linear interpolation between coarse
+ * centres and its transpose, rediscretised coarse operators, an exact
+ * separable solve on the coarsest grid.  guess (device, optional, may equal
+ * phi) is the initial phi, zero if NULL.  Stops at ||b - A phi||_2 <=
+ * rtol ||b||_2; FV_ENOCONV (stats filled) after max_iter iterations.  The
+ * hierarchy and its workspace (~6 float32 and 5 float64 cell arrays) are
+ * built on the first call and kept with the grid.  Runs on the grid's
+ * stream; returns after the last convergence check (the final mean removal
+ * is queued). */
+typedef struct {
+  double rtol;     /* relative residual target                        [1e-10] */
+  int max_iter;    /* conjugate-gradient iteration cap                  [100] */
+  int nu;          /* smoothing sweeps (each x, y, z) before and after  [1]   */
+  double omega;    /* damping of the line-Jacobi sweeps                 [0.8] */
+} fv_mg_opts;
+
+typedef struct {
+  int iterations;  /* conjugate-gradient iterations (one V-cycle each)         */
+  int levels;      /* grids of the hierarchy, the finest included              */
+  double rel_res;  /* ||b - A phi||_2 / ||b||_2 at the end                     */
+} fv_mg_stats;
+
+fv_status fv_pressure_solve_mg(fv_grid* g, const double* r, double* phi, const double* guess,
+                               const fv_mg_opts* opts, fv_mg_stats* stats);
+
 /* Allocation-free variant of fv_pressure_solve (prec = FV_MIXED) for callers
  * that cannot allocate device memory -- code running inside a memory pool it
  * does not own and may not grow, or embedded users with no access to an
@@ -419,7 +451,9 @@ typedef enum {
   FV_K_DOTS = 5,       /* weighted inner products                       */
   FV_K_VECTOR = 6,     /* other vector kernels (updates, scaling, ...)  */
   FV_K_TPF_XINV = 7,   /* pressure solve: inverse x-y transforms        */
-  FV_NKIND = 8
+  FV_K_MG_SMOOTH = 8,  /* multigrid: line-Jacobi smoothing sweeps       */
+  FV_K_MG_OTHER = 9,   /* multigrid: transfers, coarse solve, CG steps  */
+  FV_NKIND = 10
 } fv_kernel_kind;
 
 /* Start (on != 0) or stop recording; starting clears earlier records. */

@@ -40,6 +40,20 @@ int fv_host_ff_dot(int64_t n, const double* a, const double* b, double* out);
 /* Float-float arithmetic check: out = (a + b) * c, operands as (hi, lo) pairs. */
 int fv_host_ff_arith(int64_t n, const float* a, const float* b, const float* c, float* out);
 
+/* The 1-D multigrid hierarchy of fv_pressure_solve_mg along one axis with n
+ * cells and stretching map: the axis at coarsening level `level` (n_out
+ * cells; faces[n_out + 1] its faces, every other face of the level above and
+ * the last one) and the prolongation from the next coarser level to it:
+ * fine cell m takes (1 - pw1[m]) x_c[pc0[m]] + pw1[m] x_c[pc0[m] + 1]
+ * (pc0, pw1 of n_out entries; any output pointer may be NULL except n_out).
+ * An axis of at most 2 cells is not coarsened.  Returns 0 or FV_EINVAL. */
+int fv_host_mg_axis(int n, int map, int level, int* n_out, double* faces, int* pc0, double* pw1);
+
+/* Number of grids in the multigrid hierarchy of an nx x ny x nz grid (the
+ * finest included): coarsening continues while an axis has more than 4
+ * cells.  -1 on a bad size. */
+int fv_host_mg_levels(int nx, int ny, int nz);
+
 #ifdef __cplusplus
 }
 #endif

@@ -249,6 +249,29 @@ def fv_pressure_solve(g, r, phi, prec="fp64"):
                                 PRECS.get(prec, prec)), "fv_pressure_solve")
 
 
+class fv_mg_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("nu", ctypes.c_int),
+                ("omega", ctypes.c_double)]
+
+
+class fv_mg_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("levels", ctypes.c_int), ("rel_res", ctypes.c_double)]
+
+
+def fv_pressure_solve_mg(g, r, phi, guess=None, rtol=1e-10, max_iter=100, nu=1, omega=0.8,
+                         raise_on_fail=True):
+    """Multigrid-preconditioned CG pressure-correction solve (see include/fvns.h).
+    Returns the stats as a dict (status included)."""
+    o = fv_mg_opts(rtol, max_iter, nu, omega)
+    st = fv_mg_stats()
+    s = lib.fv_pressure_solve_mg(g.handle, _f64(r, g.n_cell, "r"), _f64(phi, g.n_cell, "phi"),
+                                 None if guess is None else _f64(guess, g.n_cell, "guess"),
+                                 ctypes.byref(o), ctypes.byref(st))
+    if raise_on_fail:
+        check(s, "fv_pressure_solve_mg")
+    return {"status": s, "iterations": st.iterations, "levels": st.levels, "rel_res": st.rel_res}
+
+
 def fv_pressure_solve_noalloc(shape, map, r, phi, stream=None):
     """Allocation-free float32 pressure-correction solve (see include/fvns.h)."""
     nz, ny, nx = shape
@@ -259,7 +282,8 @@ def fv_pressure_solve_noalloc(shape, map, r, phi, stream=None):
           "fv_pressure_solve_noalloc")
 
 
-KERNEL_KINDS = ["momentum", "divergence", "correct", "tpf_x", "tpf_yz", "dots", "vector", "tpf_xinv"]
+KERNEL_KINDS = ["momentum", "divergence", "correct", "tpf_x", "tpf_yz", "dots", "vector", "tpf_xinv",
+                "mg_smooth", "mg_other"]
 
 
 def fv_profile_enable(g, on=True):

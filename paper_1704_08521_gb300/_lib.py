@@ -64,6 +64,9 @@ _SIGS = {
     "fv_critical_re": (_I, [_P, _P, _P, _P, _D, _D, _P, _P, _P, _P]),
     "fv_pressure_solve": (_I, [_P, _P, _P, _I]),
     "fv_pressure_solve_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P]),
+    "fv_pressure_solve_mg": (_I, [_P, _P, _P, _P, _P, _P]),
+    "fv_host_mg_axis": (_I, [_I, _I, _I, _P, _P, _P, _P]),
+    "fv_host_mg_levels": (_I, [_I, _I, _I]),
     "fv_profile_enable": (_I, [_P, _I]),
     "fv_profile_read": (_I, [_P, _P, _P]),
     "fv_launch_count": (ctypes.c_int64, []),

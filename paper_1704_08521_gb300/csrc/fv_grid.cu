@@ -51,7 +51,7 @@ fv_status cuda_fail(cudaError_t e, const char* what, const char* file, int line)
 }
 
 // Face coordinates x_0..x_n of one axis.
-static std::vector<double> map_faces(int n, int map) {
+std::vector<double> map_faces(int n, int map) {
   std::vector<double> x(n + 1);
   const double pi = 3.14159265358979323846;
   for (int i = 0; i <= n; ++i) {
@@ -480,6 +480,7 @@ void fv_grid_destroy(fv_grid* g) {
   if (!g) return;
   for (auto& c : g->graphs) destroy_graph_cache(c);
   destroy_stokes_tables(g);
+  destroy_mg(g);
   if (g->d_arn) cudaFree(g->d_arn);
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   void* ptrs[] = {g->d_met_d, g->d_met_f, g->d_tpf_d, g->d_tpf_f, g->vel_buf[0], g->vel_buf[1],

@@ -196,6 +196,9 @@ struct fv_grid {
   int kry_cols = 0;
   double* kry_small = nullptr;   // device small-matrix area
   void* d_arn = nullptr;         // device Arnoldi area: the cycle's Hessenberg H, a scale
+
+  // multigrid pressure solve: hierarchy, level arrays, CG vectors (first use)
+  void* mg = nullptr;
 };
 
 namespace fv {
@@ -349,6 +352,14 @@ bool hess_eigenvalues(int m, const double* H, double* wr, double* wi);
 bool host_axis_tables(int n, int map, AxisBasis& B);
 // eigen-decomposition of the symmetric tridiagonal (d, e): lam, Z (n x n
 // row-major, eigenvectors as columns); implicit QR with Wilkinson shifts
+// faces x_0..x_n of an axis with n cells under the stretching map
+std::vector<double> map_faces(int n, int map);
+
+// multigrid pressure solve (built on first use, freed with the grid)
+fv_status mg_solve(fv_grid* g, const double* r, double* phi, const double* guess,
+                   const fv_mg_opts& o, fv_mg_stats* stats);
+void destroy_mg(fv_grid* g);
+
 bool sym_tridiag_eig(int n, const std::vector<double>& d, const std::vector<double>& e,
                      std::vector<double>& lam, std::vector<double>& Z);
 

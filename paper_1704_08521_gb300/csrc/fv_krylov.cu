@@ -1493,11 +1493,21 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     }
     st.gmres_total += its;
     if (!converged && o.linear != FV_LIN_GMRES && its < o.gmres_max_it) {
-      int mv = 0;
-      double rn;
-      NT_TRY(bicgstab2(g, nullptr, Fm, du, stop, o.gmres_max_it - its, cur_prec, o.sigma, o.simple_eps,
-                       pre, o.precond_sigma, &mv, &rn));
-      st.bicgstab_total += mv;
+      // BiCGstab(2) from the last approximation; after a breakdown it starts
+      // again from its best iterate (new shadow residual) while the product
+      // budget lasts and each start cuts the residual by 10 % or more
+      int budget = o.gmres_max_it - its;
+      double prev = HUGE_VAL;
+      for (int rs = 0; rs < 64 && budget > 4; ++rs) {
+        int mv = 0;
+        double rn;
+        NT_TRY(bicgstab2(g, nullptr, Fm, du, stop, budget, cur_prec, o.sigma, o.simple_eps, pre,
+                         o.precond_sigma, &mv, &rn));
+        st.bicgstab_total += mv;
+        budget -= mv;
+        if (rn <= stop || !(rn < 0.9 * prev)) break;
+        prev = rn;
+      }
     }
     NT_TRY(vec_axpby(g, nv, 1.0, U, -1.0, du, U));
   }

@@ -53,6 +53,7 @@ def main():
     ap.add_argument("--gmres-m", type=int, default=100)
     ap.add_argument("--gmres-rtol", type=float, default=1e-8)
     ap.add_argument("--gmres-sat", type=float, default=0.5)
+    ap.add_argument("--max-newton", type=int, default=30)
     ap.add_argument("--load", default="", help=".npy velocity to start the continuation from")
     ap.add_argument("--save", default="", help="write the last converged velocity here (.npy)")
     ap.add_argument("--verify", type=int, default=1)
@@ -90,7 +91,7 @@ def main():
         U_prev = U.clone()
         st = fv.newton_steady(g, U, P, tol=a.newton_tol, prec=a.prec, precond=a.precond,
                               linear=a.linear, gmres_m=a.gmres_m, gmres_sat=a.gmres_sat,
-                              gmres_max_it=20000, gmres_rtol=a.gmres_rtol, max_newton=30,
+                              gmres_max_it=20000, gmres_rtol=a.gmres_rtol, max_newton=a.max_newton,
                               raise_on_fail=False)
         t1 = sync_time()
         rec = {"re": re, "s": t1 - t0, "status": st["status"], "steps": st["iterations"],

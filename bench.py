@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-eigenpair", action="store_true",
                     help="skip the 16^3 time-to-leading-eigenpair measurement")
+    ap.add_argument("--no-mg", action="store_true", help="skip the multigrid pressure-solve measurement")
     return ap.parse_args()
 
 
@@ -246,6 +247,13 @@ def run_ours(args):
         barrier()
         ff_rate = kff / (e0.elapsed_time(e1) / 1e3)
 
+    # the multigrid pressure solve (the iterative alternative to the
+    # tensor-product solve) on this grid: D G phi = D (L_U v) to a relative
+    # residual of 1e-8, and the FP64 Krylov vector whose SIMPLE passes use it
+    mg = None
+    if mixed and not args.no_mg:
+        mg = mg_measure(fv, torch, g, U, V[0], n, stream, barrier)
+
     # one Arnoldi cycle (Krylov dimension 60: 60 Krylov vectors + CGS2 in the
     # W-inner product + the Hessenberg step) on this base flow: time per
     # Arnoldi iteration, the unit the paper's eigenvalue times are made of
@@ -420,6 +428,7 @@ def run_ours(args):
         "roofline": roof,
         "solve_roofline": solve_roof,
         "kernel_breakdown": breakdown,
+        "mg_pressure": mg,
         "clocks": clocks,
     }
     mom = prof.get("momentum")
@@ -432,6 +441,64 @@ def run_ours(args):
     if ws > 1:
         dist.destroy_process_group()
     return res
+
+
+def mg_levels(n):
+    """Cell counts of the multigrid hierarchy of an n^3 grid (coarsening of
+    every axis with more than 2 cells while one has more than 4)."""
+    m, out = n, [n ** 3]
+    while m > 4:
+        m = (m + 1) // 2 if m > 2 else m
+        out.append(m ** 3)
+    return out
+
+
+def mg_measure(fv, torch, g, U, v, n, stream, barrier, reps=5):
+    """Multigrid pressure solve at rtol 1e-8: CG iterations, ms per solve and
+    per V-cycle, and the line-smoothing sweeps' bandwidth on their
+    algorithmic bytes (x in, b in, x out: 12 B per cell per sweep; six sweeps
+    per level above the coarsest)."""
+    w = torch.empty(g.n_vel, dtype=torch.float64, device=v.device)
+    fv.ns_jacvec(g, U, v, w, prec="fp64")
+    r = torch.empty(g.n_cell, dtype=torch.float64, device=v.device)
+    fv.ns_divergence(g, w, r)
+    phi = torch.empty_like(r)
+    st = fv.fv_pressure_solve_mg(g, r, phi, rtol=1e-8)
+    barrier()
+    fv.fv_profile_enable(g, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fv.fv_pressure_solve_mg(g, r, phi, rtol=1e-8)
+    e1.record(stream)
+    barrier()
+    prof = fv.fv_profile_read(g)
+    fv.fv_profile_enable(g, False)
+    ms = e0.elapsed_time(e1) / reps
+    its = st["iterations"]
+    sm_ms, sm_n = prof["mg_smooth"]
+    lv = mg_levels(n)
+    alg_bytes = 6 * 12 * sum(lv[:-1]) * its * reps
+    peak = peaks().get("hbm_gbs", 6800.0)
+    sm_gbs = alg_bytes / (sm_ms / 1e3) / 1e9 if sm_ms > 0 else None
+    # the FP64 Krylov vector with multigrid pressure passes
+    out = torch.empty_like(v)
+    fv.simple_krylov_solve(g, None, v, out, eps=EPS, prec="fp64", pressure="mg")
+    barrier()
+    e0.record(stream)
+    for _ in range(3):
+        st2 = fv.simple_krylov_solve(g, None, v, out, eps=EPS, prec="fp64", pressure="mg")
+    e1.record(stream)
+    barrier()
+    return {"rtol": 1e-8, "levels": st["levels"], "cg_iterations": its, "ms_per_solve": ms,
+            "ms_per_vcycle_iteration": ms / max(its, 1),
+            "smooth_ms_per_solve": sm_ms / reps, "smooth_launches_per_solve": sm_n / reps,
+            "smooth_share": sm_ms / reps / ms,
+            "smooth_roofline": {"bound": "hbm", "achieved": sm_gbs, "peak": peak, "unit": "GB/s",
+                                "frac": sm_gbs / peak if sm_gbs else None,
+                                "bytes_per_cell_per_sweep": 12},
+            "fp64_krylov_vector_mg": {"solves_per_s": 3 / (e0.elapsed_time(e1) / 1e3),
+                                      "passes": st2["passes"], "pressure_rtol_per_pass": 1e-3}}
 
 
 def eigenpair_16(fv, torch, dev, synth, precs=("fp64", "mixed", "ff")):

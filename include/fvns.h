@@ -90,6 +90,11 @@ typedef struct {
   int async;      /* FV_MIXED only: 1 = do not synchronise; the call then
                      returns FV_OK once queued and stats are not filled
                      (a non-converged loop is not reported)              [0] */
+  int pressure;   /* solver of each pass's pressure correction: 0 the
+                     tensor-product factorisation, 1 the multigrid solve of
+                     fv_pressure_solve_mg (FV_FP64 only)                  [0] */
+  double pressure_rtol; /* multigrid: relative residual of each pass's
+                     solve; the later passes correct the rest          [1e-3] */
 } fv_simple_opts;
 
 typedef struct {
@@ -122,6 +127,9 @@ typedef struct {
                         far fewer operator products on strongly stretched
                         grids                                              [0] */
   double precond_sigma; /* s >= 0 of the preconditioner                    [0] */
+  int forcing;       /* 0: every correction to gmres_rtol; 1: Eisenstat-Walker
+                        forcing terms eta_k = 0.9 (||F_k|| / ||F_k-1||)^2 in
+                        [gmres_rtol, 0.1] (loose early, tight near the root) [0] */
 } fv_newton_opts;
 
 /* Section 3: the Newton corrections are computed by restarted GMRES or by
@@ -139,6 +147,9 @@ typedef struct {
   double res_hist[64];     /* ||F||_inf before each step (first 64)     */
   double res_final;
   int bicgstab_total;      /* BiCGstab(2) operator applications, summed */
+  double lin_hist[64];     /* per Newton step: the linear solver's final residual
+                              W-norm over ||F_m||_W (GMRES: its last restart's
+                              estimate; BiCGstab(2): its smallest recursive one) */
 } fv_newton_stats;
 
 typedef struct {
@@ -391,7 +402,7 @@ fv_status fv_pressure_solve(const fv_grid* g, const double* r, double* phi, int 
  * gradients in float64 on the symmetric form -V D G phi = -V r (r first made
  * compatible with the null space: r - sum(V r)/sum(V)), preconditioned by
  * one float32 V-cycle per iteration: full coarsening while an axis has more
- * than 4 cells, alternating-direction damped line-Jacobi smoothing (one
+ * than 4 cells, alternating-direction zebra line Gauss-Seidel smoothing (one
  * tridiagonal solve per grid line), linear interpolation between coarse
  * centres and its transpose, rediscretised coarse operators, an exact
  * separable solve on the coarsest grid.  guess (device, optional, may equal
@@ -405,7 +416,7 @@ typedef struct {
   double rtol;     /* relative residual target                        [1e-10] */
   int max_iter;    /* conjugate-gradient iteration cap                  [100] */
   int nu;          /* smoothing sweeps (each x, y, z) before and after  [1]   */
-  double omega;    /* damping of the line-Jacobi sweeps                 [0.8] */
+  double omega;    /* relaxation factor of the line sweeps              [1.0] */
 } fv_mg_opts;
 
 typedef struct {
@@ -451,7 +462,7 @@ typedef enum {
   FV_K_DOTS = 5,       /* weighted inner products                       */
   FV_K_VECTOR = 6,     /* other vector kernels (updates, scaling, ...)  */
   FV_K_TPF_XINV = 7,   /* pressure solve: inverse x-y transforms        */
-  FV_K_MG_SMOOTH = 8,  /* multigrid: line-Jacobi smoothing sweeps       */
+  FV_K_MG_SMOOTH = 8,  /* multigrid: line Gauss-Seidel smoothing sweeps */
   FV_K_MG_OTHER = 9,   /* multigrid: transfers, coarse solve, CG steps  */
   FV_NKIND = 10
 } fv_kernel_kind;

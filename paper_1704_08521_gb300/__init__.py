@@ -30,7 +30,8 @@ class fv_grid_info(ctypes.Structure):
 
 class fv_simple_opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_pass", ctypes.c_int), ("prec", ctypes.c_int),
-                ("omega", ctypes.c_double), ("sigma", ctypes.c_double), ("async_", ctypes.c_int)]
+                ("omega", ctypes.c_double), ("sigma", ctypes.c_double), ("async_", ctypes.c_int),
+                ("pressure", ctypes.c_int), ("pressure_rtol", ctypes.c_double)]
 
 
 class fv_simple_stats(ctypes.Structure):
@@ -44,13 +45,13 @@ class fv_newton_opts(ctypes.Structure):
                 ("prec", ctypes.c_int), ("sigma", ctypes.c_double),
                 ("simple_eps", ctypes.c_double), ("linear", ctypes.c_int),
                 ("gmres_sat", ctypes.c_double), ("precond", ctypes.c_int),
-                ("precond_sigma", ctypes.c_double)]
+                ("precond_sigma", ctypes.c_double), ("forcing", ctypes.c_int)]
 
 
 class fv_newton_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("gmres_total", ctypes.c_int),
                 ("res_hist", ctypes.c_double * 64), ("res_final", ctypes.c_double),
-                ("bicgstab_total", ctypes.c_int)]
+                ("bicgstab_total", ctypes.c_int), ("lin_hist", ctypes.c_double * 64)]
 
 
 LINEAR = {"gmres+bicgstab": 0, "gmres": 1, "bicgstab": 2}
@@ -148,9 +149,13 @@ def ns_jacvec(g, U, v, Jv, prec="fp64"):
                         _f64(Jv, g.n_vel, "Jv"), PRECS.get(prec, prec)), "ns_jacvec")
 
 
+PRESSURE = {"tpf": 0, "mg": 1}
+
+
 def simple_krylov_solve(g, U, v_in, v_out, p_out=None, eps=1e-8, max_pass=200, prec="fp64",
-                        omega=1.0, sigma=0.0, async_=False):
-    o = fv_simple_opts(eps, max_pass, PRECS.get(prec, prec), omega, sigma, 1 if async_ else 0)
+                        omega=1.0, sigma=0.0, async_=False, pressure="tpf", pressure_rtol=0.0):
+    o = fv_simple_opts(eps, max_pass, PRECS.get(prec, prec), omega, sigma, 1 if async_ else 0,
+                       PRESSURE.get(pressure, pressure), pressure_rtol)
     s = fv_simple_stats()
     check(lib.simple_krylov_solve(g.handle, None if U is None else _f64(U, g.n_vel, "U"),
                                   _f64(v_in, g.n_vel, "v_in"),
@@ -163,16 +168,17 @@ def simple_krylov_solve(g, U, v_in, v_out, p_out=None, eps=1e-8, max_pass=200, p
 
 def newton_steady(g, U, P, tol=1e-10, max_newton=30, gmres_m=100, gmres_max_it=20000,
                   gmres_rtol=1e-8, prec="fp64", sigma=10.0, simple_eps=1e-10, raise_on_fail=True,
-                  linear="gmres+bicgstab", gmres_sat=0.5, precond=0, precond_sigma=0.0):
+                  linear="gmres+bicgstab", gmres_sat=0.5, precond=0, precond_sigma=0.0, forcing=0):
     o = fv_newton_opts(tol, max_newton, gmres_m, gmres_max_it, gmres_rtol, PRECS.get(prec, prec),
                        sigma, simple_eps, LINEAR.get(linear, linear), gmres_sat, int(precond),
-                       precond_sigma)
+                       precond_sigma, int(forcing))
     s = fv_newton_stats()
     st = lib.newton_steady(g.handle, _f64(U, g.n_vel, "U"), _f64(P, g.n_cell, "P"),
                            ctypes.byref(o), ctypes.byref(s))
     out = {"status": st, "iterations": s.iterations, "gmres_total": s.gmres_total,
            "bicgstab_total": s.bicgstab_total,
-           "res_hist": list(s.res_hist[:min(s.iterations + 1, 64)]), "res_final": s.res_final}
+           "res_hist": list(s.res_hist[:min(s.iterations + 1, 64)]), "res_final": s.res_final,
+           "lin_hist": list(s.lin_hist[:min(s.iterations, 64)])}
     if raise_on_fail:
         check(st, "newton_steady")
     return out
@@ -258,7 +264,7 @@ class fv_mg_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("levels", ctypes.c_int), ("rel_res", ctypes.c_double)]
 
 
-def fv_pressure_solve_mg(g, r, phi, guess=None, rtol=1e-10, max_iter=100, nu=1, omega=0.8,
+def fv_pressure_solve_mg(g, r, phi, guess=None, rtol=1e-10, max_iter=100, nu=1, omega=1.0,
                          raise_on_fail=True):
     """Multigrid-preconditioned CG pressure-correction solve (see include/fvns.h).
     Returns the stats as a dict (status included)."""

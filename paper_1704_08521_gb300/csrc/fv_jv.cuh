@@ -337,10 +337,16 @@ __global__ void __launch_bounds__(256) k_jv_tile(Args<T, TU, TO> a) {
     for (int f = 0; f < 6; ++f) own[f] = above[f];
     if (k + 1 < k1) {
       // plane k + 2 replaces plane k in its slot; the plane kRing ahead of it
-      // goes into the ring stage it leaves
-      wait_for(last - (k + 2));                      // also: everyone is past the fluxes
+      // goes into the ring stage it leaves.  No barrier before the
+      // conversion: every thread converts exactly the ring cells whose
+      // copies it issued (its own cp.async wait covers them), nobody reads
+      // slot sc after the flux barrier above, and the barrier below orders
+      // this plane's output reads of gxs / gys before the next plane's writes
+      const int newer = last - (k + 2);
+      if (newer >= 2) cp_async_wait<2>();
+      else if (newer == 1) cp_async_wait<1>();
+      else cp_async_wait<0>();
       convert(k + 2, sc);
-      __syncthreads();
       if (last + 1 <= k1) {
         issue(last + 1);
         ++last;
@@ -348,6 +354,7 @@ __global__ void __launch_bounds__(256) k_jv_tile(Args<T, TU, TO> a) {
         cp_async_commit();                           // empty group keeps the counting uniform
         ++last;
       }
+      __syncthreads();
       T* t = sc;
       sc = sn;
       sn = t;

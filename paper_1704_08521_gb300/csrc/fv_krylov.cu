@@ -796,9 +796,11 @@ struct SimpleResult {
   double phi_first = 0.0, phi_last = 0.0, div_max = 0.0;
 };
 
+// mg (FV_FP64 only): each pass solves the pressure correction by multigrid
+// to mg->rtol instead of by the tensor-product factorisation
 static fv_status simple_loop(const fv_grid* g, double* cur, double* spare, double* out, double* p,
                              double eps, int max_pass, int prec, double omega, SimpleResult* res_out,
-                             double div_abs = 0.0) {
+                             double div_abs = 0.0, const fv_mg_opts* mg = nullptr) {
   SimpleResult local;
   SimpleResult* res = res_out ? res_out : &local;
   double* r = g->cell_buf[0];
@@ -811,7 +813,12 @@ static fv_status simple_loop(const fv_grid* g, double* cur, double* spare, doubl
   res->passes = 0;
   fv_status st = FV_ENOCONV;
   for (int pass = 1; pass <= max_pass; ++pass) {
-    FV_TRY(tpf_solve(g, r, phi, prec));
+    if (mg) {
+      fv_status ms = mg_solve(const_cast<fv_grid*>(g), r, (double*)phi, nullptr, *mg, nullptr);
+      if (ms != FV_OK && ms != FV_ENOCONV) return ms;   // a capped inexact solve is corrected later
+    } else {
+      FV_TRY(tpf_solve(g, r, phi, prec));
+    }
     FV_TRY(reset_scalars(g));
     FV_TRY(launch_correct_div(g, cur, spare, phi, prec == FV_MIXED, p, r, omega));
     std::swap(cur, spare);
@@ -1260,10 +1267,34 @@ fv_status simple_krylov_solve(const fv_grid* g, const double* U, const double* v
     set_error("simple_krylov_solve: bad option");
     return FV_EINVAL;
   }
+  if (o.pressure < 0 || o.pressure > 1 || (o.pressure == 1 && o.prec != FV_FP64) ||
+      o.pressure_rtol < 0.0 || o.pressure_rtol >= 1.0) {
+    set_error("simple_krylov_solve: bad option (pressure 1 needs FV_FP64, 0 <= pressure_rtol < 1)");
+    return FV_EINVAL;
+  }
   SimpleResult r;
+  fv_status s;
+  if (o.pressure == 1) {                       // FP64 loop with multigrid pressure solves
+    fv_mg_opts mo = {};
+    mo.rtol = o.pressure_rtol > 0.0 ? o.pressure_rtol : 1e-3;
+    mo.max_iter = 100;
+    mo.nu = 1;
+    mo.omega = 1.0;
+    FV_TRY(launch_momentum_jac(g, U ? U : g->base_ptr, v_in, v_out, FV_FP64, o.sigma));
+    s = simple_loop(g, v_out, g->vel_buf[0], v_out, p_out, o.eps, o.max_pass, FV_FP64, o.omega, &r,
+                    0.0, &mo);
+    if (s == FV_OK && o.sigma != 0.0) FV_TRY(vec_axpby(g, g->nvel, 1.0, v_out, -o.sigma, v_in, v_out));
+    if (stats) {
+      stats->passes = r.passes;
+      stats->phi_first = r.phi_first;
+      stats->phi_last = r.phi_last;
+      stats->div_max = r.div_max;
+    }
+    return s;
+  }
   const bool no_sync = o.async != 0 && o.prec != FV_FP64;
-  fv_status s = krylov_apply(g, U, v_in, v_out, p_out, o.sigma, o.prec, o.eps, o.max_pass, o.omega,
-                             no_sync ? nullptr : &r);
+  s = krylov_apply(g, U, v_in, v_out, p_out, o.sigma, o.prec, o.eps, o.max_pass, o.omega,
+                   no_sync ? nullptr : &r);
   if (stats && !no_sync) {
     stats->passes = r.passes;
     stats->phi_first = r.phi_first;
@@ -1337,8 +1368,8 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     set_error("newton_steady: bad option (gmres_m <= 128, prec, linear)");
     return FV_EINVAL;
   }
-  if (o.precond < 0 || o.precond > 1 || o.precond_sigma < 0.0) {
-    set_error("newton_steady: bad option (precond 0 or 1, precond_sigma >= 0)");
+  if (o.precond < 0 || o.precond > 1 || o.precond_sigma < 0.0 || o.forcing < 0 || o.forcing > 1) {
+    set_error("newton_steady: bad option (precond 0 or 1, precond_sigma >= 0, forcing 0 or 1)");
     return FV_EINVAL;
   }
   const bool pre = o.precond == 1;            // flexible GMRES(m) with the stored M^-1 v_j
@@ -1365,7 +1396,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
   // step, then float64 (the inexact Jacobian of the mixed form limits the
   // linear rate of Newton near the root); the residual is always float64
   int cur_prec = o.prec;
-  double prev_res = -1.0;
+  double prev_res = -1.0, eta_prev = 0.1;
   // errors inside the iteration still report the steps taken
 #define NT_TRY(x)                                   \
   do {                                              \
@@ -1409,8 +1440,22 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     }
     if (it == o.max_newton) break;
     if (cur_prec == FV_MIXED && prev_res > 0.0 && res > 0.1 * prev_res) cur_prec = FV_FP64;
+    // relative tolerance of this correction: fixed, or the Eisenstat-Walker
+    // forcing term (their choice 2: gamma 0.9, exponent 2, with its safeguard)
+    double eta = o.gmres_rtol;
+    if (o.forcing == 1) {
+      double e = 0.1;
+      if (prev_res > 0.0) {
+        const double q = res / prev_res;
+        e = 0.9 * q * q;
+        const double safe = 0.9 * eta_prev * eta_prev;
+        if (safe > 0.1) e = std::max(e, safe);
+      }
+      eta = std::min(0.1, std::max(e, o.gmres_rtol));
+      eta_prev = eta;
+    }
     prev_res = res;
-    const double lin_rtol = cur_prec == FV_MIXED ? std::max(o.gmres_rtol, 1e-6) : o.gmres_rtol;
+    const double lin_rtol = cur_prec == FV_MIXED ? std::max(eta, 1e-6) : eta;
     // the Jacobian of this step: U converted once for all its Krylov vectors
     NT_TRY(set_base(g, U));
 
@@ -1423,6 +1468,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     int its = 0;
     bool first = true, converged = false;
     double prev_beta = bnorm;
+    double lin_res = bnorm;                    // latest residual estimate of this correction
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol(m + 2);
     while (o.linear != FV_LIN_BICGSTAB) {
       // r = b - A du
@@ -1437,6 +1483,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       double beta;
       NT_TRY(dot_host(g, V, V, &beta));
       beta = std::sqrt(beta);
+      lin_res = beta;
       if (beta <= stop) { converged = true; break; }
       if (its >= o.gmres_max_it) break;
       // saturated: the last restart cycle cut the residual by less than gmres_sat
@@ -1490,6 +1537,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
                               g->stream));
       NT_TRY(vec_update(g, du, pre ? Z : V, nv, jdone, g->kry_small, 1.0, cur_prec != FV_FP64));
       NT_CUDA(cudaStreamSynchronize(g->stream));
+      lin_res = std::fabs(gv[jdone]);
     }
     st.gmres_total += its;
     if (!converged && o.linear != FV_LIN_GMRES && its < o.gmres_max_it) {
@@ -1505,10 +1553,12 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
                          o.precond_sigma, &mv, &rn));
         st.bicgstab_total += mv;
         budget -= mv;
+        lin_res = std::min(lin_res, rn);
         if (rn <= stop || !(rn < 0.9 * prev)) break;
         prev = rn;
       }
     }
+    if (it < 64) st.lin_hist[it] = bnorm > 0.0 ? lin_res / bnorm : 0.0;
     NT_TRY(vec_axpby(g, nv, 1.0, U, -1.0, du, U));
   }
 #undef NT_TRY

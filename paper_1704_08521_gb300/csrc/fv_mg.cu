@@ -23,12 +23,14 @@
 // interpolation between coarse cell centres in the stretched coordinate,
 // constant beyond the first and last centre (the Neumann walls).
 // Restriction: its transpose, so the integrated residual is conserved.
-// Smoother: damped block Jacobi over grid lines, alternating the line
-// direction -- the cosine-stretched grids have cells with aspect ratios of
-// tens, for which point smoothers fail and line smoothers do not; each
-// line's tridiagonal system is solved by the Thomas recurrence, one thread
-// per line.  Pre-smoothing sweeps x, y, z and post-smoothing z, y, x with
-// the same damping, so the V-cycle is a symmetric preconditioner.  Coarsest
+// Smoother: zebra line Gauss-Seidel, alternating the line direction -- the
+// cosine-stretched grids have cells with aspect ratios of tens, for which
+// point smoothers fail and line smoothers do not.  Each half-sweep solves
+// every line of one colour (lines coloured like a checkerboard of their two
+// transverse indices, so neighbour lines differ in colour) by the Thomas
+// recurrence, one thread per line, in place.  Pre-smoothing x, y, z (colours
+// 0, 1) and post-smoothing in the exact reverse order, so the V-cycle is a
+// symmetric preconditioner.  Coarsest
 // level (at most 4 cells per axis): exact solve by the separable eigenbases
 // of the coarse operator (A = sum over axes of K_d (x) W_others, K_d E_d =
 // W_d E_d Lambda_d), null mode dropped.
@@ -190,29 +192,39 @@ __device__ __forceinline__ T apply_at(const Lv& L, const T* __restrict__ x, int 
 }
 
 // --------------------------------------------------------- V-cycle kernels --
-// One damped block-Jacobi sweep over the lines along axis D:
-//   xout = xin + omega * D_D^-1 (b - A xin),
-// D_D the tridiagonal part of A along D.  One thread per line; the Thomas
-// recurrence keeps its c' and d' in cb / db (same indexing as the cells).
+// One half-sweep of zebra line Gauss-Seidel along axis D: every line along
+// D of colour `color` (the parity of its two transverse indices' sum) is
+// solved exactly for the current values of its neighbour lines, which all
+// have the other colour and are not written by this launch:
+//   x_line += omega * D_line^-1 (b - A x)_line,
+// D_line the tridiagonal part of A along the line.  In place.  One thread per
+// line; the Thomas recurrence keeps its c' and d' in cb / db (same indexing
+// as the cells).  Transverse indices: a (the faster one: i for y- and
+// z-lines, j for x-lines) and b (k for x- and y-lines, j for z-lines); the
+// thread's line has a = 2 t_a + ((b + color) & 1).
 template <int D>
-__global__ void __launch_bounds__(128) k_line(LevDev L, const float* __restrict__ xin,
-                                              const float* __restrict__ b, float* __restrict__ xout,
-                                              float* __restrict__ cb, float* __restrict__ db,
-                                              float omega) {
+__global__ void __launch_bounds__(128) k_line(LevDev L, float* __restrict__ x,
+                                              const float* __restrict__ b, float* __restrict__ cb,
+                                              float* __restrict__ db, float omega, int color) {
   const int nx = L.n[0], ny = L.n[1];
   const int nl = L.n[D];
-  const int64_t nlines = L.ncell / nl;
-  const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (line >= nlines) return;
+  const int na = D == 0 ? ny : nx;
+  const int nb = D == 2 ? ny : L.n[2];
+  const int ha = (na + 1) >> 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ha * nb) return;
+  const int tb = (int)(t / ha);
+  const int ta = 2 * (int)(t - (int64_t)tb * ha) + ((tb + color) & 1);
+  if (ta >= na) return;
   // first cell of the line and the stride along it
   int i0, j0, k0;
   int64_t stride;
   if (D == 0) {
-    i0 = 0; j0 = (int)(line % ny); k0 = (int)(line / ny); stride = 1;
+    i0 = 0; j0 = ta; k0 = tb; stride = 1;
   } else if (D == 1) {
-    i0 = (int)(line % nx); j0 = 0; k0 = (int)(line / nx); stride = nx;
+    i0 = ta; j0 = 0; k0 = tb; stride = nx;
   } else {
-    i0 = (int)(line % nx); j0 = (int)(line / nx); k0 = 0; stride = (int64_t)nx * ny;
+    i0 = ta; j0 = tb; k0 = 0; stride = (int64_t)nx * ny;
   }
   const int64_t c00 = ((int64_t)k0 * ny + j0) * nx + i0;
   const float* tD = L.t[D];
@@ -231,7 +243,7 @@ __global__ void __launch_bounds__(128) k_line(LevDev L, const float* __restrict_
         const int i = D == 0 ? m : i0, j = D == 1 ? m : j0, k = D == 2 ? m : k0;
         const int64_t c = c00 + (int64_t)m * stride;
         float diag;
-        const float ax = apply_at<float>(L, xin, i, j, k, c, &diag);
+        const float ax = apply_at<float>(L, x, i, j, k, c, &diag);
         res[u] = b[c] - ax;
         dg[u] = diag;
       }
@@ -262,7 +274,7 @@ __global__ void __launch_bounds__(128) k_line(LevDev L, const float* __restrict_
         const int64_t c = c00 + (int64_t)m * stride;
         cc[u] = cb[c];
         dd[u] = db[c];
-        xi[u] = xin[c];
+        xi[u] = x[c];
       }
     }
 #pragma unroll
@@ -271,7 +283,7 @@ __global__ void __launch_bounds__(128) k_line(LevDev L, const float* __restrict_
       if (m >= 0) {
         const int64_t c = c00 + (int64_t)m * stride;
         const float del = dd[u] - cc[u] * dn;
-        xout[c] = xi[u] + omega * del;
+        x[c] = xi[u] + omega * del;
         dn = del;
       }
     }
@@ -745,30 +757,32 @@ fv_status vcycle(const fv_grid* g, MgState* M, int l, int nu, float omega, cudaS
     return FV_OK;
   }
   FV_CUDA(cudaMemsetAsync(H.x[0], 0, L.ncell * sizeof(float), st));
-  int cur = 0;
-  auto sweep = [&](int D) -> fv_status {
-    const int64_t nlines = L.ncell / L.n[D];
-    const int nb = (int)((nlines + 127) / 128);
-    float* xin = H.x[cur];
-    float* xout = H.x[cur ^ 1];
-    if (D == 0) k_line<0><<<nb, 128, 0, st>>>(L, xin, H.b, xout, H.cb, H.db, omega);
-    else if (D == 1) k_line<1><<<nb, 128, 0, st>>>(L, xin, H.b, xout, H.cb, H.db, omega);
-    else MG_LAUNCH(FV_K_MG_SMOOTH, k_line<2><<<nb, 128, 0, st>>>(L, xin, H.b, xout, H.cb, H.db, omega));
-    cur ^= 1;
+  float* x = H.x[0];
+  auto sweep = [&](int D, int color) -> fv_status {
+    const int na = D == 0 ? L.n[1] : L.n[0];
+    const int nb = D == 2 ? L.n[1] : L.n[2];
+    const int64_t nthr = (int64_t)((na + 1) / 2) * nb;
+    const int nblk = (int)((nthr + 127) / 128);
+    if (D == 0) MG_LAUNCH(FV_K_MG_SMOOTH, k_line<0><<<nblk, 128, 0, st>>>(L, x, H.b, H.cb, H.db, omega, color));
+    else if (D == 1) MG_LAUNCH(FV_K_MG_SMOOTH, k_line<1><<<nblk, 128, 0, st>>>(L, x, H.b, H.cb, H.db, omega, color));
+    else MG_LAUNCH(FV_K_MG_SMOOTH, k_line<2><<<nblk, 128, 0, st>>>(L, x, H.b, H.cb, H.db, omega, color));
     return FV_OK;
   };
+  // symmetric Gauss-Seidel: x, y, z (colours 0, 1) before, the exact reverse after
   for (int s = 0; s < nu; ++s)
-    for (int D = 0; D < 3; ++D) FV_TRY(sweep(D));
+    for (int D = 0; D < 3; ++D)
+      for (int c = 0; c < 2; ++c) FV_TRY(sweep(D, c));
   const MgLevelHost& C = M->lev[l + 1];
-  MG_LAUNCH(FV_K_MG_OTHER, k_resid32<<<blocks_for(L.ncell), 256, 0, st>>>(L, H.x[cur], H.b, H.res));
+  MG_LAUNCH(FV_K_MG_OTHER, k_resid32<<<blocks_for(L.ncell), 256, 0, st>>>(L, x, H.b, H.res));
   MG_LAUNCH(FV_K_MG_OTHER, k_restrict<<<blocks_for(C.dev.ncell), 256, 0, st>>>(L, C.dev.n[0], C.dev.n[1], C.dev.n[2], H.res,
                                                     C.b));
   FV_TRY(vcycle(g, M, l + 1, nu, omega, st));
   MG_LAUNCH(FV_K_MG_OTHER, k_prolong_add<<<blocks_for(L.ncell), 256, 0, st>>>(L, C.dev.n[0], C.dev.n[1], C.x[C.cur],
-                                                     H.x[cur]));
+                                                     x));
   for (int s = 0; s < nu; ++s)
-    for (int D = 2; D >= 0; --D) FV_TRY(sweep(D));
-  H.cur = cur;
+    for (int D = 2; D >= 0; --D)
+      for (int c = 1; c >= 0; --c) FV_TRY(sweep(D, c));
+  H.cur = 0;
   return FV_OK;
 }
 
@@ -883,7 +897,7 @@ extern "C" fv_status fv_pressure_solve_mg(fv_grid* g, const double* r, double* p
   if (o.rtol <= 0) o.rtol = 1e-10;
   if (o.max_iter <= 0) o.max_iter = 100;
   if (o.nu <= 0) o.nu = 1;
-  if (o.omega <= 0) o.omega = 0.8;
+  if (o.omega <= 0) o.omega = 1.0;
   if (o.nu > 8 || o.omega >= 2.0) {
     set_error("fv_pressure_solve_mg: bad option (nu <= 8, 0 < omega < 2)");
     return FV_EINVAL;

@@ -11,7 +11,9 @@ fv_unet_train_step (forward, backward, Adam on the device).
 Evaluation at larger grids on held-out directions: the relative error of
 the guess, and SIMPLE passes and device time of one Krylov-vector
 evaluation (eps = 1e-8) with the plain loop (exact first pass) against the
-loop whose first pass is the guess.
+loop whose first pass is the guess; and conjugate-gradient iterations and
+device time of the multigrid pressure solve (relative residual --mg-rtol)
+from zero against the same solve started from the guess.
 
     python -m paper_1704_08521_gb300.unet_train --train 64,80,96,112,128 \
         --steps 600 --eval 200,256 --rhs 4 [--save params.npy]
@@ -77,6 +79,7 @@ def main(argv=None):
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--save", default=None)
+    ap.add_argument("--mg-rtol", type=float, default=1e-8)
     a = ap.parse_args(argv)
 
     import torch
@@ -143,10 +146,21 @@ def main(argv=None):
                     g, U, v, out, eps=a.eps, prec="mixed"))
                 ms_guess, st_guess = timed(torch, lambda: fv.simple_krylov_solve_guess(
                     g, net, U, v, out, eps=a.eps, prec="mixed"))
-                ms_tpf, _ = timed(torch, lambda: fv.fv_pressure_solve(g, r, phi, prec="mixed"))
+                phi_tpf = torch.empty_like(phi)
+                ms_tpf, _ = timed(torch, lambda: fv.fv_pressure_solve(g, r, phi_tpf, prec="mixed"))
+                # the multigrid pressure solve to rtol from zero and from the guess
+                phi_mg = torch.empty_like(phi)
+                ms_mg0, st_mg0 = timed(torch, lambda: fv.fv_pressure_solve_mg(g, r, phi_mg, rtol=a.mg_rtol))
+
+                def mg_from_guess():
+                    net.guess(g, r, guess)
+                    return fv.fv_pressure_solve_mg(g, r, phi_mg, guess=guess, rtol=a.mg_rtol)
+                ms_mg1, st_mg1 = timed(torch, mg_from_guess)
                 rows.append({"guess_rel_err": err, "guess_rel_err_max": err_max, "passes_plain": st_plain["passes"],
                              "passes_guess": st_guess["passes"], "ms_plain": ms_plain,
-                             "ms_guess": ms_guess, "ms_net": ms_guess_only, "ms_exact_solve": ms_tpf})
+                             "ms_guess": ms_guess, "ms_net": ms_guess_only, "ms_exact_solve": ms_tpf,
+                             "mg_iters_zero": st_mg0["iterations"], "mg_iters_guess": st_mg1["iterations"],
+                             "ms_mg_zero": ms_mg0, "ms_mg_guess": ms_mg1})
             agg = {key: float(np.mean([row[key] for row in rows])) for key in rows[0]}
             # exact solves the loop needed: plain = passes; guess = passes - 1
             agg["exact_solves_saved"] = agg["passes_plain"] - (agg["passes_guess"] - 1)

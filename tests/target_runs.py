@@ -5,9 +5,11 @@ Not collected by pytest (a GPU run of minutes): run it on a GB300 as
         --eig-re 1900 --m 60 --nev 10 --out result.json
 
 Steps (Section 3):
-1. steady states by Newton continuation in Re from rest on the n^3 cosine
-   grid (newton_steady, float-float Krylov vectors, the Stokes-type right
-   preconditioner of the corrections, ||F||_inf < tol);
+1. steady states by Newton continuation in Re from rest (or from a saved
+   state) on the n^3 grid (newton_steady, float-float Krylov vectors, the
+   Stokes-type right preconditioner of the corrections, ||F||_inf < tol);
+   each stage starts from the secant extrapolation of the last two
+   converged states, and a failed stage is retried at half the Re step;
 2. at each Re of --eig-re the leading eigenvalues by implicitly restarted
    Arnoldi in regular mode (arnoldi_leading) from the seeded Gaussian start
    vector;
@@ -54,8 +56,15 @@ def main():
     ap.add_argument("--gmres-rtol", type=float, default=1e-8)
     ap.add_argument("--gmres-sat", type=float, default=0.5)
     ap.add_argument("--max-newton", type=int, default=30)
+    ap.add_argument("--precond-sigma", type=float, default=0.0)
+    ap.add_argument("--load-re", type=float, default=0.0, help="Re of the --load state")
+    ap.add_argument("--predictor", type=int, default=1, help="secant predictor in Re")
+    ap.add_argument("--forcing", type=int, default=0, help="1: Eisenstat-Walker linear tolerances")
+    ap.add_argument("--halvings", type=int, default=3, help="Re-step halvings after a failed stage")
     ap.add_argument("--load", default="", help=".npy velocity to start the continuation from")
     ap.add_argument("--save", default="", help="write the last converged velocity here (.npy)")
+    ap.add_argument("--save-at", default="", help="Re values whose states also go to --save-pattern")
+    ap.add_argument("--save-pattern", default="", help="path with {re}")
     ap.add_argument("--verify", type=int, default=1)
     ap.add_argument("--out", default="target_run.json")
     a = ap.parse_args()
@@ -70,6 +79,7 @@ def main():
     eig_re = [float(x) for x in a.eig_re.split(",") if x]
     res = {"n": n, "map": a.map, "alpha_deg": a.alpha, "prec": a.prec, "precond": a.precond,
            "linear": a.linear, "gmres_m": a.gmres_m, "gmres_rtol": a.gmres_rtol, "load": a.load,
+           "precond_sigma": a.precond_sigma, "forcing": a.forcing, "predictor": a.predictor,
            "newton": [], "arnoldi": [], "critical": None, "verify": {}}
     dev = torch.device("cuda")
     g = fv.Grid(n, n, n, a.map, alpha=alpha, re=path[0])
@@ -85,24 +95,47 @@ def main():
         torch.cuda.synchronize()
         return time.perf_counter()
 
-    for re in path:
+    # continuation: a secant predictor from the last two converged states,
+    # and a halved Re step (up to --halvings times) after a failed stage
+    conv = []                                   # (re, U) of the last converged states
+    if a.load:
+        conv.append((a.load_re, U.clone()))
+    queue = list(path)
+    halvings = 0
+    while queue:
+        re = queue[0]
         g.set_re(re)
-        t0 = sync_time()
         U_prev = U.clone()
+        if len(conv) >= 2 and a.predictor:
+            (r0, U0), (r1, U1) = conv[-2], conv[-1]
+            U.copy_(U1 + (U1 - U0) * ((re - r1) / (r1 - r0)))
+        t0 = sync_time()
         st = fv.newton_steady(g, U, P, tol=a.newton_tol, prec=a.prec, precond=a.precond,
+                              precond_sigma=a.precond_sigma, forcing=a.forcing,
                               linear=a.linear, gmres_m=a.gmres_m, gmres_sat=a.gmres_sat,
                               gmres_max_it=20000, gmres_rtol=a.gmres_rtol, max_newton=a.max_newton,
                               raise_on_fail=False)
         t1 = sync_time()
         rec = {"re": re, "s": t1 - t0, "status": st["status"], "steps": st["iterations"],
-               "products": st["gmres_total"] + st["bicgstab_total"], "res": st["res_hist"]}
+               "products": st["gmres_total"] + st["bicgstab_total"], "res": st["res_hist"],
+               "lin": st["lin_hist"], "predicted": len(conv) >= 2 and a.predictor}
         res["newton"].append(rec)
         print(json.dumps(rec), flush=True)
         if st["status"] != 0:
             U.copy_(U_prev)
+            if halvings < a.halvings and conv:
+                halvings += 1
+                queue.insert(0, 0.5 * (conv[-1][0] + re))
+                continue
             break
+        queue.pop(0)
+        if re in path:
+            halvings = 0
+        conv = (conv + [(re, U.clone())])[-2:]
         if a.save:
             np.save(a.save, U.cpu().numpy())
+        if a.save_pattern and re in [float(x) for x in a.save_at.split(",") if x]:
+            np.save(a.save_pattern.replace("{re}", f"{re:g}"), U.cpu().numpy())
         if re in eig_re:
             states[re] = U.clone()
             t0 = sync_time()

@@ -130,6 +130,18 @@ typedef struct {
   int forcing;       /* 0: every correction to gmres_rtol; 1: Eisenstat-Walker
                         forcing terms eta_k = 0.9 (||F_k|| / ||F_k-1||)^2 in
                         [gmres_rtol, 0.1] (loose early, tight near the root) [0] */
+  int gmres_aug;     /* precond = 1: the last gmres_aug (<= 4) steps of each
+                        flexible GMRES cycle take the corrections of the
+                        previous cycles as their directions (the LGMRES
+                        augmentation of Baker, Jessup & Manteuffel 2005,
+                        against the stagnation of restarted GMRES)        [0] */
+  double tau;        /* >= 0: each correction solves (A - tau I) du = F
+                        instead of A du = F (a shifted, pseudo-transient
+                        Newton step: same steady state; error modes of
+                        eigenvalue lambda contract by tau / |lambda - tau|
+                        per step; moves the weakly damped oscillatory
+                        modes near the imaginary axis away from it, where
+                        restarted Krylov solvers stagnate)                [0] */
 } fv_newton_opts;
 
 /* Section 3: the Newton corrections are computed by restarted GMRES or by
@@ -257,6 +269,9 @@ typedef struct {
   double newton_tol;  /* ||F||_inf of each steady state                  [1e-10] */
   double arnoldi_tol; /* Ritz tolerance                                  [1e-10] */
   int precond;        /* fv_newton_opts.precond of the steady states          [0] */
+  double precond_sigma; /* fv_newton_opts.precond_sigma                       [0] */
+  int forcing;        /* fv_newton_opts.forcing                                [0] */
+  int max_restarts;   /* fv_arnoldi_opts.max_restarts (0: its default)         [0] */
 } fv_critical_opts;
 
 typedef struct {

@@ -45,7 +45,8 @@ class fv_newton_opts(ctypes.Structure):
                 ("prec", ctypes.c_int), ("sigma", ctypes.c_double),
                 ("simple_eps", ctypes.c_double), ("linear", ctypes.c_int),
                 ("gmres_sat", ctypes.c_double), ("precond", ctypes.c_int),
-                ("precond_sigma", ctypes.c_double), ("forcing", ctypes.c_int)]
+                ("precond_sigma", ctypes.c_double), ("forcing", ctypes.c_int),
+                ("gmres_aug", ctypes.c_int), ("tau", ctypes.c_double)]
 
 
 class fv_newton_stats(ctypes.Structure):
@@ -168,10 +169,11 @@ def simple_krylov_solve(g, U, v_in, v_out, p_out=None, eps=1e-8, max_pass=200, p
 
 def newton_steady(g, U, P, tol=1e-10, max_newton=30, gmres_m=100, gmres_max_it=20000,
                   gmres_rtol=1e-8, prec="fp64", sigma=10.0, simple_eps=1e-10, raise_on_fail=True,
-                  linear="gmres+bicgstab", gmres_sat=0.5, precond=0, precond_sigma=0.0, forcing=0):
+                  linear="gmres+bicgstab", gmres_sat=0.5, precond=0, precond_sigma=0.0, forcing=0,
+                  gmres_aug=0, tau=0.0):
     o = fv_newton_opts(tol, max_newton, gmres_m, gmres_max_it, gmres_rtol, PRECS.get(prec, prec),
                        sigma, simple_eps, LINEAR.get(linear, linear), gmres_sat, int(precond),
-                       precond_sigma, int(forcing))
+                       precond_sigma, int(forcing), int(gmres_aug), float(tau))
     s = fv_newton_stats()
     st = lib.newton_steady(g.handle, _f64(U, g.n_vel, "U"), _f64(P, g.n_cell, "P"),
                            ctypes.byref(o), ctypes.byref(s))
@@ -201,7 +203,9 @@ def arnoldi_leading(g, U, v0, m=30, nev=5, evec=None, tol=1e-10, max_restarts=50
 class fv_critical_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("m", ctypes.c_int),
                 ("nev", ctypes.c_int), ("prec", ctypes.c_int), ("newton_tol", ctypes.c_double),
-                ("arnoldi_tol", ctypes.c_double), ("precond", ctypes.c_int)]
+                ("arnoldi_tol", ctypes.c_double), ("precond", ctypes.c_int),
+                ("precond_sigma", ctypes.c_double), ("forcing", ctypes.c_int),
+                ("max_restarts", ctypes.c_int)]
 
 
 class fv_critical_stats(ctypes.Structure):
@@ -210,10 +214,11 @@ class fv_critical_stats(ctypes.Structure):
 
 
 def fv_critical_re(g, U, P, v0, re0, re1, rtol=1e-8, max_iter=30, m=30, nev=4, prec="fp64",
-                   newton_tol=1e-10, arnoldi_tol=1e-10, precond=0):
+                   newton_tol=1e-10, arnoldi_tol=1e-10, precond=0, precond_sigma=0.0, forcing=0,
+                   max_restarts=0):
     """Secant search of Re_cr (Section 3); returns (re_cr, omega_cr, history)."""
     o = fv_critical_opts(rtol, max_iter, m, nev, PRECS.get(prec, prec), newton_tol, arnoldi_tol,
-                         int(precond))
+                         int(precond), precond_sigma, int(forcing), int(max_restarts))
     s = fv_critical_stats()
     rc, om = ctypes.c_double(), ctypes.c_double()
     check(lib.fv_critical_re(g.handle, _f64(U, g.n_vel, "U"), _f64(P, g.n_cell, "P"),

@@ -30,11 +30,14 @@
 // Values outside the domain (beyond a wall) load as zero: the homogeneous
 // wall value of the diffusive flux, and a zero transport velocity.
 //
-// Block: (TXo + 1) x (TYo + 1) threads, one flux position each; the outputs
-// are the TXo x TYo positions that have both their high neighbours in the
-// tile.  Shared memory: two plane slots of the six fields on the
-// (TXo + 2) x (TYo + 2) tile with a one-cell halo, and the exchanged x/y
-// fluxes.  Raw planes arrive through a cp.async ring issued three planes ahead.
+// Block: one thread per cell of the (TXo + 2) x (TYo + 2) tile (the outputs
+// and a one-cell halo); each thread copies and converts its own cell of every
+// plane.  The threads of the (TXo + 1) x (TYo + 1) cells past the low halo
+// row and column compute the fluxes through their cells' low faces, and the
+// TXo x TYo of them whose high neighbours are in the tile form the outputs.
+// Shared memory: two plane slots of the six fields on the tile and the
+// exchanged x/y fluxes.  Raw planes arrive through a cp.async ring issued
+// three planes ahead.
 // U is read in its stored form (the grid's registered base flow, walls
 // zeroed); x is the caller's float64 vector, rounded / split when a plane is
 // converted.
@@ -118,18 +121,28 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // computed and the plane above it.
 constexpr int kRing = 3;
 
+constexpr int kJvMaxThreads = 320;   // threads (= tile cells) per block, at most
+
+// resident blocks per SM the register budget is sized for: three for the
+// float32 form (63 registers), two for the float64 and float-float forms,
+// whose fluxes need more registers
+template <typename T> struct MinBlocks { static constexpr int value = 3; };
+template <> struct MinBlocks<double> { static constexpr int value = 2; };
+template <> struct MinBlocks<ffn> { static constexpr int value = 2; };
+
 template <typename T, typename TU, typename TO>
-__global__ void __launch_bounds__(256) k_jv_tile(Args<T, TU, TO> a) {
+__global__ void __launch_bounds__(kJvMaxThreads, MinBlocks<T>::value) k_jv_tile(Args<T, TU, TO> a) {
   extern __shared__ __align__(16) unsigned char jv_smem[];
   const Met<T>& m = a.m;
   const int nx = m.n[0], ny = m.n[1], nz = m.n[2];
   const int nc = (int)m.ncell;
   const int TXo = a.t.txo, TYo = a.t.tyo;
-  const int TXf = TXo + 1;
   const int LX = TXo + 2, LY = TYo + 2, LXY = LX * LY;
-  const int nthr = blockDim.x;
+  const int nthr = blockDim.x;                               // == LXY
   const int tid = threadIdx.x;
-  const int tx = tid % TXf, ty = tid / TXf;
+  const int li = tid % LX, lj = tid / LX;                    // this thread's tile cell
+  const int tx = li - 1, ty = lj - 1;                        // its flux position
+  const bool flux_thr = li >= 1 && lj >= 1;
   const int i0 = blockIdx.x * TXo, j0 = blockIdx.y * TYo;
   const int k0 = blockIdx.z * a.t.kz;
   const int k1 = min(k0 + a.t.kz, nz);
@@ -149,52 +162,28 @@ __global__ void __launch_bounds__(256) k_jv_tile(Args<T, TU, TO> a) {
   if (a.call) X = a.call->x;
   const TU* Ur = a.Ur;
 
-  // tile cells of this thread (at most two: the tile has < 2 nthr cells)
-  int cb[2];
-  bool cin[2];
-  int cij[2][2];
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int e = tid + r * nthr;
-    const int li = e % LX, lj = e / LX;
-    const int ci = i0 - 1 + li, cj = j0 - 1 + lj;
-    cij[r][0] = ci;
-    cij[r][1] = cj;
-    cin[r] = e < LXY && ci >= 0 && ci < nx && cj >= 0 && cj < ny;
-    cb[r] = cin[r] ? cj * nx + ci : 0;
-  }
+  // this thread's tile cell in the plane
+  const int ci = i0 - 1 + li, cj = j0 - 1 + lj;
+  const bool cin = ci >= 0 && ci < nx && cj >= 0 && cj < ny;
+  const int cb = cin ? cj * nx + ci : 0;
   auto issue = [&](int k) {                 // plane k -> ring stage (k + 1) % kRing
     const int st = (k + 1 + kRing) % kRing;
-    const bool kin = k >= 0 && k < nz;
+    const bool v = cin && k >= 0 && k < nz;
+    const int b = v ? k * (nx * ny) + cb : 0;
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int e = tid + r * nthr;
-      if (e < LXY) {
-        const bool v = cin[r] && kin;
-        const int b = v ? k * (nx * ny) + cb[r] : 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          cp_async_v<sizeof(TU)>(ru(st) + c * LXY + e, Ur + c * nc + b, v);
-          cp_async_v<8>(rx(st) + c * LXY + e, X + c * nc + b, v);
-        }
-      }
+    for (int c = 0; c < 3; ++c) {
+      cp_async_v<sizeof(TU)>(ru(st) + c * LXY + tid, Ur + c * nc + b, v);
+      cp_async_v<8>(rx(st) + c * LXY + tid, X + c * nc + b, v);
     }
     cp_async_commit();
   };
   auto convert = [&](int k, T* s) {         // ring stage of plane k -> slot s (walls zero)
     const int st = (k + 1 + kRing) % kRing;
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int e = tid + r * nthr;
-      if (e < LXY) {
-        const int ci = cij[r][0], cj = cij[r][1];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const bool wall = (c == 0 && ci == 0) || (c == 1 && cj == 0) || (c == 2 && k == 0);
-          s[c * LXY + e] = wall ? T(0) : conv<T, TU>(ru(st)[c * LXY + e]);
-          s[(3 + c) * LXY + e] = wall ? T(0) : conv<T, double>(rx(st)[c * LXY + e]);
-        }
-      }
+    for (int c = 0; c < 3; ++c) {
+      const bool wall = (c == 0 && ci == 0) || (c == 1 && cj == 0) || (c == 2 && k == 0);
+      s[c * LXY + tid] = wall ? T(0) : conv<T, TU>(ru(st)[c * LXY + tid]);
+      s[(3 + c) * LXY + tid] = wall ? T(0) : conv<T, double>(rx(st)[c * LXY + tid]);
     }
   };
   // wait until plane k's copies (issued before the `newer` later planes) landed
@@ -206,11 +195,13 @@ __global__ void __launch_bounds__(256) k_jv_tile(Args<T, TU, TO> a) {
   };
 
   // tile offsets of this thread's position and its low neighbours
-  const int o0 = (ty + 1) * LX + (tx + 1);
-  const int oxm = o0 - 1, oym = o0 - LX;
+  const int o0 = tid;
+  // low neighbours; the halo row / column threads read their own cell instead
+  // (their fluxes are computed but never read)
+  const int oxm = flux_thr ? o0 - 1 : o0, oym = flux_thr ? o0 - LX : o0;
 
   // per-thread metrics (x from fi, y from fj; clamped where unused)
-  const int fic = min(fi, nx), fjc = min(fj, ny);
+  const int fic = min(max(fi, 0), nx), fjc = min(max(fj, 0), ny);
   const T idc_x = m.idc[0][fic], th_x = m.th[0][fic];
   const T idxm_x = m.idx[0][max(fic - 1, 0)];
   const T idx_x = m.idx[0][min(fic, nx - 1)];
@@ -220,7 +211,7 @@ __global__ void __launch_bounds__(256) k_jv_tile(Args<T, TU, TO> a) {
   const T inv_re = a.inv_re;
   const T half = T(0.5);
 
-  const bool out_thr = tx < TXo && ty < TYo && fi < nx && fj < ny;
+  const bool out_thr = flux_thr && tx < TXo && ty < TYo && fi < nx && fj < ny;
 
   // z-fluxes through the face between planes kf - 1 (below, "zm") and kf
   // ("cz" = own column values of plane kf); the w neighbours along x and y
@@ -312,7 +303,7 @@ __global__ void __launch_bounds__(256) k_jv_tile(Args<T, TU, TO> a) {
     zflux(above, own, sn, k + 1, gz_hi, ez_hi);
     __syncthreads();
     if (out_thr) {
-      const int hx = tid + 1, hy = tid + TXf;       // high x / y neighbours in the flux tile
+      const int hx = tid + 1, hy = tid + LX;        // high x / y neighbours in the tile
       const T idx_z = m.idx[2][k], idc_z = m.idc[2][k];
       const int b = (k * ny + fj) * nx + fi;
       T wu = T(0), wv = T(0), ww = T(0);
@@ -363,16 +354,18 @@ __global__ void __launch_bounds__(256) k_jv_tile(Args<T, TU, TO> a) {
   cp_async_wait<0>();
 }
 
-// Launch shape of a grid: tiles as square as 256 flux threads allow, sized
-// to split nx and ny evenly (little idle tail), and z-chunks so that the
-// blocks fill the resident slots of the 152 SMs (`per_sm` blocks each) once:
-// a second partial wave would double the time of the chunk.
-inline Tile tile_shape(const int n[3], int per_sm = 4) {
+// Launch shape of a grid: tiles of at most kJvMaxThreads cells (outputs plus
+// the one-cell halo) sized to split nx and ny evenly (little idle tail), and
+// z-chunks so that the blocks fill the resident slots of the 152 SMs
+// (`per_sm` blocks each) once: a second partial wave would double the time
+// of the chunk.
+
+inline Tile tile_shape(const int n[3], int per_sm = 3) {
   Tile t;
-  const int ntx = (n[0] + 30) / 31;                  // at most 31 outputs (32 threads) along x
+  const int ntx = (n[0] + 30) / 31;                  // at most 31 outputs (33 cells) along x
   t.txo = (n[0] + ntx - 1) / ntx;
-  const int tyf_max = 256 / (t.txo + 1);
-  const int nty = (n[1] + tyf_max - 2) / (tyf_max - 1);
+  const int ly_max = kJvMaxThreads / (t.txo + 2);    // tile rows, halo included
+  const int nty = (n[1] + ly_max - 3) / (ly_max - 2);
   t.tyo = (n[1] + nty - 1) / nty;
   const int64_t xy = (int64_t)ntx * nty;
   const int64_t slots = 152 * (int64_t)(per_sm < 1 ? 1 : per_sm);
@@ -388,7 +381,7 @@ inline dim3 tile_grid(const int n[3], const Tile& t) {
               (unsigned)((n[2] + t.kz - 1) / t.kz));
 }
 
-inline int tile_threads(const Tile& t) { return (t.txo + 1) * (t.tyo + 1); }
+inline int tile_threads(const Tile& t) { return (t.txo + 2) * (t.tyo + 2); }
 
 template <typename T, typename TU>
 inline size_t tile_smem(const Tile& t) {

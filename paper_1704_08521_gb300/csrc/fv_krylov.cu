@@ -1112,7 +1112,7 @@ static fv_status maxabs_host(const fv_grid* g, int64_t n, const double* x, doubl
 // at the end (one more preconditioner application, no product).
 static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double* x, double stop,
                            int max_mv, int prec, double sigma, double eps, bool pre, double psig,
-                           int* mv, double* rnorm_out) {
+                           double tau, int* mv, double* rnorm_out) {
   const int64_t nv = g->nvel;
   double* rt = g->kry;
   double* r[3] = {g->kry + nv, g->kry + 2 * nv, g->kry + 3 * nv};
@@ -1120,9 +1120,11 @@ static fv_status bicgstab2(fv_grid* g, const double* U, const double* b, double*
   double* xbest = g->kry + 7 * nv;
   double* yit = g->kry + 8 * nv;             // preconditioned iterate
   double* tz = g->kry + 9 * nv;              // M^-1 of the vector being applied
-  auto plain = [&](const double* in, double* out) {
+  auto plain = [&](const double* in, double* out) -> fv_status {   // out = (A - tau I) in
     ++*mv;
-    return krylov_apply(g, U, in, out, nullptr, sigma, prec, eps, 200, 1.0, nullptr);
+    FV_TRY(krylov_apply(g, U, in, out, nullptr, sigma, prec, eps, 200, 1.0, nullptr));
+    if (tau != 0.0) FV_TRY(vec_axpby(g, nv, 1.0, out, -tau, in, out));
+    return FV_OK;
   };
   auto apply = [&](const double* in, double* out) -> fv_status {
     if (pre) {
@@ -1368,13 +1370,19 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     set_error("newton_steady: bad option (gmres_m <= 128, prec, linear)");
     return FV_EINVAL;
   }
-  if (o.precond < 0 || o.precond > 1 || o.precond_sigma < 0.0 || o.forcing < 0 || o.forcing > 1) {
-    set_error("newton_steady: bad option (precond 0 or 1, precond_sigma >= 0, forcing 0 or 1)");
+  if (o.precond < 0 || o.precond > 1 || o.precond_sigma < 0.0 || o.forcing < 0 || o.forcing > 1 ||
+      !(o.tau >= 0.0)) {
+    set_error("newton_steady: bad option (precond 0 or 1, precond_sigma >= 0, forcing 0 or 1, tau >= 0)");
     return FV_EINVAL;
   }
   const bool pre = o.precond == 1;            // flexible GMRES(m) with the stored M^-1 v_j
   const int m = o.gmres_m;
-  FV_TRY(ensure_krylov(g, pre ? std::max(2 * m + 1, 10) : std::max(m + 1, 8)));
+  const int naug_max = pre ? o.gmres_aug : 0;  // augmentation vectors of the flexible cycles
+  if (o.gmres_aug < 0 || o.gmres_aug > 4 || (o.gmres_aug > 0 && (!pre || o.gmres_aug >= m))) {
+    set_error("newton_steady: bad option (gmres_aug in [0, 4], < gmres_m, needs precond = 1)");
+    return FV_EINVAL;
+  }
+  FV_TRY(ensure_krylov(g, pre ? std::max(2 * m + 1 + naug_max + 1, 10) : std::max(m + 1, 8)));
   {
     int w;                                     // forget statuses of earlier evaluations
     FV_TRY(graph_take_status(g, &w, false));
@@ -1382,6 +1390,10 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
   const int64_t nv = g->nvel;
   double* V = g->kry;
   double* Z = pre ? g->kry + (int64_t)(m + 1) * nv : nullptr;   // preconditioned directions
+  // the corrections of the latest restart cycles (unit W-norm), the newest
+  // in aug[(aug_head - 1) mod (naug_max + 1)]; one slot more holds the
+  // correction being formed
+  double* aug = pre ? g->kry + (int64_t)(2 * m + 1) * nv : nullptr;
   double* Fm = g->vel_buf[1];
   double* du = g->vel_buf[2];
   fv_newton_stats st = {};
@@ -1469,6 +1481,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
     bool first = true, converged = false;
     double prev_beta = bnorm;
     double lin_res = bnorm;                    // latest residual estimate of this correction
+    int naug = 0, aug_head = 0;                // augmentation vectors of this solve
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol(m + 2);
     while (o.linear != FV_LIN_BICGSTAB) {
       // r = b - A du
@@ -1477,6 +1490,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       } else {
         NT_TRY(krylov_apply(g, nullptr, du, V, nullptr, o.sigma, cur_prec, o.simple_eps, 200, 1.0,
                             nullptr));
+        if (o.tau != 0.0) NT_TRY(vec_axpby(g, nv, 1.0, V, -o.tau, du, V));
         NT_TRY(vec_axpby(g, nv, -1.0, V, 1.0, Fm, V));
       }
       first = false;
@@ -1498,11 +1512,19 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
         const double* vj = V + (int64_t)j * nv;
         if (pre) {                             // z_j = M^-1 v_j, w = A z_j
           double* zj = Z + (int64_t)j * nv;
-          NT_TRY(stokes_precond_apply(g, vj, zj, o.precond_sigma));
+          const int ja = j - (m - naug);           // the last naug steps take earlier corrections
+          if (ja >= 0) {
+            const int slot = ((aug_head - 1 - ja) % (naug_max + 1) + (naug_max + 1)) % (naug_max + 1);
+            NT_CUDA(cudaMemcpyAsync(zj, aug + (int64_t)slot * nv, nv * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, g->stream));
+          } else {
+            NT_TRY(stokes_precond_apply(g, vj, zj, o.precond_sigma));
+          }
           vj = zj;
         }
         NT_TRY(krylov_apply(g, nullptr, vj, w, nullptr, o.sigma, cur_prec, o.simple_eps,
                             200, 1.0, nullptr));
+        if (o.tau != 0.0) NT_TRY(vec_axpby(g, nv, 1.0, w, -o.tau, vj, w));
         double hn;
         NT_TRY(cgs2(g, V, j + 1, w, hcol.data(), &hn, cur_prec != FV_FP64));
         if (hn > 0) NT_TRY(vec_axpby(g, nv, 1.0 / hn, w, 0.0, nullptr, w));
@@ -1535,7 +1557,23 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
       }
       NT_CUDA(cudaMemcpyAsync(g->kry_small, y.data(), jdone * sizeof(double), cudaMemcpyHostToDevice,
                               g->stream));
-      NT_TRY(vec_update(g, du, pre ? Z : V, nv, jdone, g->kry_small, 1.0, cur_prec != FV_FP64));
+      if (naug_max > 0) {
+        // this cycle's correction Z y, kept (normalised) for the next cycles
+        double* dc = aug + (int64_t)aug_head * nv;
+        NT_CUDA(cudaMemsetAsync(dc, 0, nv * sizeof(double), g->stream));
+        NT_TRY(vec_update(g, dc, Z, nv, jdone, g->kry_small, 1.0, cur_prec != FV_FP64));
+        NT_TRY(vec_axpby(g, nv, 1.0, du, 1.0, dc, du));
+        double dn;
+        NT_TRY(dot_host(g, dc, dc, &dn));
+        dn = std::sqrt(dn);
+        if (dn > 0.0 && std::isfinite(dn)) {
+          NT_TRY(vec_axpby(g, nv, 1.0 / dn, dc, 0.0, nullptr, dc));
+          aug_head = (aug_head + 1) % (naug_max + 1);
+          naug = std::min(naug + 1, naug_max);
+        }
+      } else {
+        NT_TRY(vec_update(g, du, pre ? Z : V, nv, jdone, g->kry_small, 1.0, cur_prec != FV_FP64));
+      }
       NT_CUDA(cudaStreamSynchronize(g->stream));
       lin_res = std::fabs(gv[jdone]);
     }
@@ -1550,7 +1588,7 @@ fv_status newton_steady(fv_grid* g, double* U, double* P, const fv_newton_opts* 
         int mv = 0;
         double rn;
         NT_TRY(bicgstab2(g, nullptr, Fm, du, stop, budget, cur_prec, o.sigma, o.simple_eps, pre,
-                         o.precond_sigma, &mv, &rn));
+                         o.precond_sigma, o.tau, &mv, &rn));
         st.bicgstab_total += mv;
         budget -= mv;
         lin_res = std::min(lin_res, rn);
@@ -1801,9 +1839,12 @@ fv_status fv_critical_re(fv_grid* g, double* U, double* P, const double* v0, dou
   no.tol = o.newton_tol;
   no.prec = o.prec;
   no.precond = o.precond;
+  no.precond_sigma = o.precond_sigma;
+  no.forcing = o.forcing;
   fv_arnoldi_opts ao = {};
   ao.tol = o.arnoldi_tol;
   ao.prec = o.prec;
+  ao.max_restarts = o.max_restarts;
   std::vector<double> lr(o.nev), li(o.nev);
   // sigma(Re): Newton from the current U, P, then the leading eigenvalue
   auto sigma = [&](double re, double* s, double* w) -> fv_status {

@@ -60,6 +60,8 @@ def main():
     ap.add_argument("--load-re", type=float, default=0.0, help="Re of the --load state")
     ap.add_argument("--predictor", type=int, default=1, help="secant predictor in Re")
     ap.add_argument("--forcing", type=int, default=0, help="1: Eisenstat-Walker linear tolerances")
+    ap.add_argument("--gmres-aug", type=int, default=0, help="augmentation vectors of flexible GMRES")
+    ap.add_argument("--tau", type=float, default=0.0, help="shift of the Newton corrections")
     ap.add_argument("--halvings", type=int, default=3, help="Re-step halvings after a failed stage")
     ap.add_argument("--load", default="", help=".npy velocity to start the continuation from")
     ap.add_argument("--save", default="", help="write the last converged velocity here (.npy)")
@@ -80,6 +82,7 @@ def main():
     res = {"n": n, "map": a.map, "alpha_deg": a.alpha, "prec": a.prec, "precond": a.precond,
            "linear": a.linear, "gmres_m": a.gmres_m, "gmres_rtol": a.gmres_rtol, "load": a.load,
            "precond_sigma": a.precond_sigma, "forcing": a.forcing, "predictor": a.predictor,
+           "gmres_aug": a.gmres_aug, "tau": a.tau,
            "newton": [], "arnoldi": [], "critical": None, "verify": {}}
     dev = torch.device("cuda")
     g = fv.Grid(n, n, n, a.map, alpha=alpha, re=path[0])
@@ -112,7 +115,7 @@ def main():
         t0 = sync_time()
         st = fv.newton_steady(g, U, P, tol=a.newton_tol, prec=a.prec, precond=a.precond,
                               precond_sigma=a.precond_sigma, forcing=a.forcing,
-                              linear=a.linear, gmres_m=a.gmres_m, gmres_sat=a.gmres_sat,
+                              gmres_aug=a.gmres_aug, tau=a.tau, linear=a.linear, gmres_m=a.gmres_m, gmres_sat=a.gmres_sat,
                               gmres_max_it=20000, gmres_rtol=a.gmres_rtol, max_newton=a.max_newton,
                               raise_on_fail=False)
         t1 = sync_time()
@@ -158,7 +161,9 @@ def main():
         try:
             rc, om, hist = fv.fv_critical_re(g, U, P, v0, r0, r1, rtol=a.secant_rtol, m=a.m,
                                              nev=a.nev, prec=a.prec, newton_tol=a.newton_tol,
-                                             arnoldi_tol=a.arnoldi_tol, precond=a.precond)
+                                             arnoldi_tol=a.arnoldi_tol, precond=a.precond,
+                                             precond_sigma=a.precond_sigma, forcing=a.forcing,
+                                             max_restarts=a.max_restarts)
             res["critical"] = {"re_cr": rc, "omega_cr": om, "hist": hist}
         except fv.FvError as e:
             res["critical"] = {"error": str(e)}

@@ -150,3 +150,47 @@ def test_bad_precond_option(fv):
         fv.newton_steady(g, U, P, precond=2)
     with pytest.raises(fv.FvError):
         fv.newton_steady(g, U, P, precond=1, precond_sigma=-1.0)
+
+
+def test_augmented_flexible_gmres_same_steady_state(fv):
+    """Flexible GMRES(10) whose last two steps per cycle take the previous
+    cycles' corrections (LGMRES augmentation) reaches the stored oracle
+    steady state of the 16^3 continuation to 1e-9; the option is refused
+    without the preconditioner or beyond 4 vectors."""
+    gold = np.load(GOLD)
+    g = fv.Grid(16, 16, 16, "cosine", alpha=0.0, re=200.0)
+    U = torch.zeros(g.n_vel, dtype=torch.float64, device="cuda")
+    P = torch.zeros(g.n_cell, dtype=torch.float64, device="cuda")
+    for re in (200.0, 400.0, 600.0, 800.0, 1000.0):
+        g.set_re(re)
+        fv.newton_steady(g, U, P, tol=1e-10, prec="ff", linear="gmres", gmres_m=10, precond=1,
+                         gmres_aug=2)
+    torch.cuda.synchronize()
+    ref = gold["U"]
+    assert np.abs(U.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-9
+    with pytest.raises(fv.FvError):
+        fv.newton_steady(g, U, P, gmres_aug=2)
+    with pytest.raises(fv.FvError):
+        fv.newton_steady(g, U, P, precond=1, gmres_aug=5)
+
+
+def test_shifted_newton_same_steady_state(fv):
+    """Corrections from (A - tau I) du = F (tau = 0.1) converge to the same
+    stored oracle steady state of the 16^3 continuation, to 1e-9: the shift
+    changes the path, not the fixed point."""
+    gold = np.load(GOLD)
+    g = fv.Grid(16, 16, 16, "cosine", alpha=0.0, re=200.0)
+    U = torch.zeros(g.n_vel, dtype=torch.float64, device="cuda")
+    P = torch.zeros(g.n_cell, dtype=torch.float64, device="cuda")
+    steps = 0
+    for re in (200.0, 400.0, 600.0, 800.0, 1000.0):
+        g.set_re(re)
+        st = fv.newton_steady(g, U, P, tol=1e-10, prec="ff", precond=1, precond_sigma=1.0,
+                              tau=0.1, max_newton=60)
+        steps += st["iterations"]
+    torch.cuda.synchronize()
+    ref = gold["U"]
+    assert np.abs(U.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-9
+    with pytest.raises(fv.FvError):
+        fv.newton_steady(g, U, P, tau=-1.0)
+    print(f"\n16^3 continuation with tau = 0.1: {steps} Newton steps")

@@ -272,6 +272,8 @@ typedef struct {
   double precond_sigma; /* fv_newton_opts.precond_sigma                       [0] */
   int forcing;        /* fv_newton_opts.forcing                                [0] */
   int max_restarts;   /* fv_arnoldi_opts.max_restarts (0: its default)         [0] */
+  double tau;         /* fv_newton_opts.tau                                    [0] */
+  int max_newton;     /* fv_newton_opts.max_newton (0: its default)            [0] */
 } fv_critical_opts;
 
 typedef struct {

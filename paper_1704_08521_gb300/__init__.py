@@ -205,7 +205,7 @@ class fv_critical_opts(ctypes.Structure):
                 ("nev", ctypes.c_int), ("prec", ctypes.c_int), ("newton_tol", ctypes.c_double),
                 ("arnoldi_tol", ctypes.c_double), ("precond", ctypes.c_int),
                 ("precond_sigma", ctypes.c_double), ("forcing", ctypes.c_int),
-                ("max_restarts", ctypes.c_int)]
+                ("max_restarts", ctypes.c_int), ("tau", ctypes.c_double), ("max_newton", ctypes.c_int)]
 
 
 class fv_critical_stats(ctypes.Structure):
@@ -215,10 +215,11 @@ class fv_critical_stats(ctypes.Structure):
 
 def fv_critical_re(g, U, P, v0, re0, re1, rtol=1e-8, max_iter=30, m=30, nev=4, prec="fp64",
                    newton_tol=1e-10, arnoldi_tol=1e-10, precond=0, precond_sigma=0.0, forcing=0,
-                   max_restarts=0):
+                   max_restarts=0, tau=0.0, max_newton=0):
     """Secant search of Re_cr (Section 3); returns (re_cr, omega_cr, history)."""
     o = fv_critical_opts(rtol, max_iter, m, nev, PRECS.get(prec, prec), newton_tol, arnoldi_tol,
-                         int(precond), precond_sigma, int(forcing), int(max_restarts))
+                         int(precond), precond_sigma, int(forcing), int(max_restarts), float(tau),
+                         int(max_newton))
     s = fv_critical_stats()
     rc, om = ctypes.c_double(), ctypes.c_double()
     check(lib.fv_critical_re(g.handle, _f64(U, g.n_vel, "U"), _f64(P, g.n_cell, "P"),

@@ -1841,6 +1841,8 @@ fv_status fv_critical_re(fv_grid* g, double* U, double* P, const double* v0, dou
   no.precond = o.precond;
   no.precond_sigma = o.precond_sigma;
   no.forcing = o.forcing;
+  no.tau = o.tau;
+  no.max_newton = o.max_newton;
   fv_arnoldi_opts ao = {};
   ao.tol = o.arnoldi_tol;
   ao.prec = o.prec;

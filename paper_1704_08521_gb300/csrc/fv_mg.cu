@@ -290,6 +290,190 @@ __global__ void __launch_bounds__(128) k_line(LevDev L, float* __restrict__ x,
   }
 }
 
+// The same half-sweep with each line split over P warps (the partition
+// method for tridiagonal systems): a block owns 32 lines of the colour (one
+// per lane) and P segments of each (one per warp).  Segment p of a line has
+// rows [s, e) and couples to the rows s - 1 and e of its neighbours only
+// through its first row's lower and its last row's upper coefficient.
+//  1. forward over the segment: residuals r_m (kept in shared memory), the
+//     inverse pivots 1/den_m of the segment's own tridiagonal matrix T (kept),
+//     and the last rows of y = T^-1 r, v = T^-1 e_first, w = T^-1 e_last;
+//  2. the same elimination from the bottom: the first rows of y, v, w;
+//  3. warp 0 solves, per line, the 2P boundary unknowns (first and last row
+//     of each segment): a block-tridiagonal system with 2 x 2 blocks;
+//  4. each segment solves T x = r - (coupling to the neighbours' boundary
+//     values) with the kept pivots and adds omega x to the line.
+// Shared memory: r and the pivots as [row][lane] (conflict-free), the
+// boundary values [P][8][lane].
+template <int D>
+__global__ void __launch_bounds__(256) k_line_part(LevDev L, float* __restrict__ x,
+                                                   const float* __restrict__ b, float omega,
+                                                   int color, int P) {
+  extern __shared__ float ps[];
+  const int nx = L.n[0], ny = L.n[1];
+  const int nl = L.n[D];
+  const int na = D == 0 ? ny : nx;
+  const int nb = D == 2 ? ny : L.n[2];
+  const int ha = (na + 1) >> 1;
+  const int lane = threadIdx.x & 31, p = threadIdx.x >> 5;
+  float* R = ps;                    // [nl][32]
+  float* Q = ps + nl * 32;          // [nl][32] inverse pivots
+  float* S = Q + nl * 32;           // [P][8][32]
+  const int64_t t = (int64_t)blockIdx.x * 32 + lane;
+  bool valid = t < (int64_t)ha * nb;
+  int ta = 0, tb = 0;
+  if (valid) {
+    tb = (int)(t / ha);
+    ta = 2 * (int)(t - (int64_t)tb * ha) + ((tb + color) & 1);
+    valid = ta < na;
+  }
+  int i0, j0, k0;
+  int64_t stride;
+  if (D == 0) {
+    i0 = 0; j0 = ta; k0 = tb; stride = 1;
+  } else if (D == 1) {
+    i0 = ta; j0 = 0; k0 = tb; stride = nx;
+  } else {
+    i0 = ta; j0 = tb; k0 = 0; stride = (int64_t)nx * ny;
+  }
+  const int64_t c00 = ((int64_t)k0 * ny + j0) * nx + i0;
+  const float* tD = L.t[D];
+  const float wa = valid ? (D == 0 ? L.w[1][j0] : L.w[0][i0]) : 0.f;
+  const float wb = valid ? (D == 2 ? L.w[1][j0] : L.w[2][k0]) : 0.f;
+  const float cross = wa * wb;
+  const int s0 = (int)(((int64_t)p * nl) / P), e0 = (int)(((int64_t)(p + 1) * nl) / P);
+  // coefficient of row m: lower -cross t[m], upper -cross t[m + 1]; the
+  // diagonal is A's (all six faces)
+  auto diag_at = [&](int m) {       // the expression apply_at evaluates
+    const int i = D == 0 ? m : i0, j = D == 1 ? m : j0, k = D == 2 ? m : k0;
+    const float wx = L.w[0][i], wy = L.w[1][j], wz = L.w[2][k];
+    const float ax0 = wy * wz * L.t[0][i], ax1 = wy * wz * L.t[0][i + 1];
+    const float ay0 = wx * wz * L.t[1][j], ay1 = wx * wz * L.t[1][j + 1];
+    const float az0 = wx * wy * L.t[2][k], az1 = wx * wy * L.t[2][k + 1];
+    return ax0 + ax1 + ay0 + ay1 + az0 + az1;
+  };
+  float yl = 0.f, vl = 0.f, wl = 0.f, yf = 0.f, vf = 0.f, wf = 0.f;
+  const float lext = -cross * tD[s0], uext = -cross * tD[e0];
+  if (valid) {
+    // 1. forward
+    float dy = 0.f, dv = 0.f, dw = 0.f, cprev = 0.f;
+    constexpr int U = 4;
+    for (int m0 = s0; m0 < e0; m0 += U) {
+      float res[U], dg[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int m = m0 + u;
+        if (m < e0) {
+          const int i = D == 0 ? m : i0, j = D == 1 ? m : j0, k = D == 2 ? m : k0;
+          const int64_t c = c00 + (int64_t)m * stride;
+          float dgv;
+          const float ax = apply_at<float>(L, x, i, j, k, c, &dgv);
+          res[u] = b[c] - ax;
+          dg[u] = dgv;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int m = m0 + u;
+        if (m < e0) {
+          const float lo = m > s0 ? -cross * tD[m] : 0.f;
+          const float up = m < e0 - 1 ? -cross * tD[m + 1] : 0.f;
+          const float inv = 1.f / (dg[u] - lo * cprev);
+          dy = (res[u] - lo * dy) * inv;
+          dv = ((m == s0 ? 1.f : 0.f) - lo * dv) * inv;
+          dw = ((m == e0 - 1 ? 1.f : 0.f) - lo * dw) * inv;
+          cprev = up * inv;
+          R[m * 32 + lane] = res[u];
+          Q[m * 32 + lane] = inv;
+        }
+      }
+    }
+    yl = dy; vl = dv; wl = dw;
+    // 2. the same elimination from the bottom row up
+    float ry = 0.f, rv = 0.f, rw = 0.f, gprev = 0.f;
+    for (int m = e0 - 1; m >= s0; --m) {
+      const float lo = m > s0 ? -cross * tD[m] : 0.f;
+      const float up = m < e0 - 1 ? -cross * tD[m + 1] : 0.f;
+      const float inv = 1.f / (diag_at(m) - up * gprev);
+      const float r = R[m * 32 + lane];
+      ry = (r - up * ry) * inv;
+      rv = ((m == s0 ? 1.f : 0.f) - up * rv) * inv;
+      rw = ((m == e0 - 1 ? 1.f : 0.f) - up * rw) * inv;
+      gprev = lo * inv;
+    }
+    yf = ry; vf = rv; wf = rw;
+  }
+  float* Sp = S + (p * 8) * 32 + lane;
+  Sp[0 * 32] = yf; Sp[1 * 32] = yl; Sp[2 * 32] = vf; Sp[3 * 32] = vl;
+  Sp[4 * 32] = wf; Sp[5 * 32] = wl; Sp[6 * 32] = lext; Sp[7 * 32] = uext;
+  __syncthreads();
+  // 3. boundary unknowns X_q = (a_q, b_q) (first, last row of segment q):
+  //    A_q X_{q-1} + X_q + C_q X_{q+1} = Y_q, A_q = lext_q [0 v_f; 0 v_l],
+  //    C_q = uext_q [w_f 0; w_l 0]; block elimination, then back-substitution
+  if (p == 0 && valid) {
+    float Ch[8][4], Yh[8][2];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (q < P) {
+        const float* Sq = S + (q * 8) * 32 + lane;
+        const float qyf = Sq[0], qyl = Sq[32], qvf = Sq[64], qvl = Sq[96];
+        const float qwf = Sq[128], qwl = Sq[160], ql = Sq[192], qu = Sq[224];
+        // B = I - A_q Ch_{q-1}; A_q has only a second column (lext v_f, lext v_l)
+        float b00 = 1.f, b01 = 0.f, b10 = 0.f, b11 = 1.f, y0 = qyf, y1 = qyl;
+        if (q > 0) {
+          const float a0 = ql * qvf, a1 = ql * qvl;        // A_q = [0 a0; 0 a1]
+          // A_q Ch = [a0 Ch[1][:]; a1 Ch[1][:]] (row 1 of Ch: entries 2, 3)
+          b00 -= a0 * Ch[q - 1][2]; b01 -= a0 * Ch[q - 1][3];
+          b10 -= a1 * Ch[q - 1][2]; b11 -= a1 * Ch[q - 1][3];
+          y0 -= a0 * Yh[q - 1][1];
+          y1 -= a1 * Yh[q - 1][1];
+        }
+        const float det = b00 * b11 - b01 * b10;
+        const float i00 = b11 / det, i01 = -b01 / det, i10 = -b10 / det, i11 = b00 / det;
+        // C_q = [c0 0; c1 0] with c0 = uext w_f, c1 = uext w_l
+        const float c0 = qu * qwf, c1 = qu * qwl;
+        Ch[q][0] = i00 * c0 + i01 * c1; Ch[q][1] = 0.f;
+        Ch[q][2] = i10 * c0 + i11 * c1; Ch[q][3] = 0.f;
+        Yh[q][0] = i00 * y0 + i01 * y1;
+        Yh[q][1] = i10 * y0 + i11 * y1;
+      }
+    }
+    float xa = 0.f;                  // a_{q+1}
+#pragma unroll
+    for (int q = 7; q >= 0; --q) {
+      if (q < P) {
+        const float a = Yh[q][0] - Ch[q][0] * xa;
+        const float bq = Yh[q][1] - Ch[q][2] * xa;
+        S[(q * 8 + 0) * 32 + lane] = a;     // first row of segment q
+        S[(q * 8 + 1) * 32 + lane] = bq;    // last row of segment q
+        xa = a;
+      }
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  // 4. the segment's rows from its modified right-hand side
+  const float xprev = p > 0 ? S[((p - 1) * 8 + 1) * 32 + lane] : 0.f;
+  const float xnext = p < P - 1 ? S[((p + 1) * 8 + 0) * 32 + lane] : 0.f;
+  float d = 0.f;
+  for (int m = s0; m < e0; ++m) {
+    const float lo = m > s0 ? -cross * tD[m] : 0.f;
+    float rhs = R[m * 32 + lane];
+    if (m == s0) rhs -= lext * xprev;
+    if (m == e0 - 1) rhs -= uext * xnext;
+    d = (rhs - lo * d) * Q[m * 32 + lane];
+    R[m * 32 + lane] = d;
+  }
+  float dn = 0.f;
+  for (int m = e0 - 1; m >= s0; --m) {
+    const float up = m < e0 - 1 ? -cross * tD[m + 1] : 0.f;
+    const float del = R[m * 32 + lane] - up * Q[m * 32 + lane] * dn;
+    const int64_t c = c00 + (int64_t)m * stride;
+    x[c] += omega * del;
+    dn = del;
+  }
+}
+
 __global__ void k_resid32(LevDev L, const float* __restrict__ x, const float* __restrict__ b,
                           float* __restrict__ res) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell;
@@ -739,6 +923,24 @@ fv_status build_mg(fv_grid* g) {
   return FV_OK;
 }
 
+// lines of at most this many cells take the partitioned kernel (its shared
+// memory grows with the line)
+constexpr int kPartMaxLine = 640;
+
+size_t part_smem(int nl, int P) { return sizeof(float) * ((size_t)2 * nl * 32 + (size_t)P * 8 * 32); }
+
+fv_status set_part_attributes() {
+  static bool done = false;
+  if (!done) {
+    const int bytes = (int)part_smem(kPartMaxLine, 8);
+    FV_CUDA(cudaFuncSetAttribute(k_line_part<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    FV_CUDA(cudaFuncSetAttribute(k_line_part<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    FV_CUDA(cudaFuncSetAttribute(k_line_part<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done = true;
+  }
+  return FV_OK;
+}
+
 // a launch, timed under `kind` by the grid's profiler and counted
 #define MG_LAUNCH(kind, ...)          \
   do {                                \
@@ -761,8 +963,18 @@ fv_status vcycle(const fv_grid* g, MgState* M, int l, int nu, float omega, cudaS
   auto sweep = [&](int D, int color) -> fv_status {
     const int na = D == 0 ? L.n[1] : L.n[0];
     const int nb = D == 2 ? L.n[1] : L.n[2];
-    const int64_t nthr = (int64_t)((na + 1) / 2) * nb;
-    const int nblk = (int)((nthr + 127) / 128);
+    const int64_t nlines = (int64_t)((na + 1) / 2) * nb;
+    const int nl = L.n[D];
+    if (nl <= kPartMaxLine) {     // lines split over P warps, 32 lines per block
+      const int P = std::max(1, std::min(8, nl / 12));
+      const int nblk = (int)((nlines + 31) / 32);
+      const size_t sm = part_smem(nl, P);
+      if (D == 0) MG_LAUNCH(FV_K_MG_SMOOTH, k_line_part<0><<<nblk, 32 * P, sm, st>>>(L, x, H.b, omega, color, P));
+      else if (D == 1) MG_LAUNCH(FV_K_MG_SMOOTH, k_line_part<1><<<nblk, 32 * P, sm, st>>>(L, x, H.b, omega, color, P));
+      else MG_LAUNCH(FV_K_MG_SMOOTH, k_line_part<2><<<nblk, 32 * P, sm, st>>>(L, x, H.b, omega, color, P));
+      return FV_OK;
+    }
+    const int nblk = (int)((nlines + 127) / 128);
     if (D == 0) MG_LAUNCH(FV_K_MG_SMOOTH, k_line<0><<<nblk, 128, 0, st>>>(L, x, H.b, H.cb, H.db, omega, color));
     else if (D == 1) MG_LAUNCH(FV_K_MG_SMOOTH, k_line<1><<<nblk, 128, 0, st>>>(L, x, H.b, H.cb, H.db, omega, color));
     else MG_LAUNCH(FV_K_MG_SMOOTH, k_line<2><<<nblk, 128, 0, st>>>(L, x, H.b, H.cb, H.db, omega, color));
@@ -789,6 +1001,7 @@ fv_status vcycle(const fv_grid* g, MgState* M, int l, int nu, float omega, cudaS
 // z = M^-1 r: round r into level 0, one V-cycle, widen
 fv_status precondition(fv_grid* g, MgState* M, const double* r, double* z, int nu, float omega) {
   cudaStream_t st = g->stream;
+  FV_TRY(set_part_attributes());
   MgLevelHost& H = M->lev[0];
   MG_LAUNCH(FV_K_MG_OTHER, k_round_cells<<<blocks_for(g->ncell), 256, 0, st>>>(g->ncell, r, H.b));
   FV_TRY(vcycle(g, M, 0, nu, omega, st));

@@ -163,7 +163,8 @@ def main():
                                              nev=a.nev, prec=a.prec, newton_tol=a.newton_tol,
                                              arnoldi_tol=a.arnoldi_tol, precond=a.precond,
                                              precond_sigma=a.precond_sigma, forcing=a.forcing,
-                                             max_restarts=a.max_restarts)
+                                             max_restarts=a.max_restarts, tau=a.tau,
+                                             max_newton=a.max_newton)
             res["critical"] = {"re_cr": rc, "omega_cr": om, "hist": hist}
         except fv.FvError as e:
             res["critical"] = {"error": str(e)}

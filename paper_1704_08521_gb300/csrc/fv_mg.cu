@@ -966,7 +966,8 @@ fv_status vcycle(const fv_grid* g, MgState* M, int l, int nu, float omega, cudaS
     const int64_t nlines = (int64_t)((na + 1) / 2) * nb;
     const int nl = L.n[D];
     if (nl <= kPartMaxLine) {     // lines split over P warps, 32 lines per block
-      const int P = std::max(1, std::min(8, nl / 12));
+      // segments of >= 4 rows: short chains on the coarse levels too
+      const int P = std::max(1, std::min(8, nl / 4));
       const int nblk = (int)((nlines + 31) / 32);
       const size_t sm = part_smem(nl, P);
       if (D == 0) MG_LAUNCH(FV_K_MG_SMOOTH, k_line_part<0><<<nblk, 32 * P, sm, st>>>(L, x, H.b, omega, color, P));

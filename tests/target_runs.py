@@ -66,6 +66,7 @@ def main():
     ap.add_argument("--load", default="", help=".npy velocity to start the continuation from")
     ap.add_argument("--save", default="", help="write the last converged velocity here (.npy)")
     ap.add_argument("--save-at", default="", help="Re values whose states also go to --save-pattern")
+    ap.add_argument("--save-evec", default="", help="write the leading eigenvector (re, im) here (.npy)")
     ap.add_argument("--save-pattern", default="", help="path with {re}")
     ap.add_argument("--verify", type=int, default=1)
     ap.add_argument("--out", default="target_run.json")
@@ -155,6 +156,8 @@ def main():
             print(json.dumps(rec), flush=True)
             if ok:
                 states[("evec", re)] = (evec.clone(), lam[0])
+                if a.save_evec:
+                    np.save(a.save_evec, evec.cpu().numpy())
     if a.secant and res["newton"] and res["newton"][-1]["status"] == 0:
         r0, r1 = [float(x) for x in a.secant.split(",")]
         t0 = sync_time()

@@ -27,10 +27,12 @@
 // cosine-stretched grids have cells with aspect ratios of tens, for which
 // point smoothers fail and line smoothers do not.  Each half-sweep solves
 // every line of one colour (lines coloured like a checkerboard of their two
-// transverse indices, so neighbour lines differ in colour) by the Thomas
-// recurrence, one thread per line, in place.  Pre-smoothing x, y, z (colours
-// 0, 1) and post-smoothing in the exact reverse order, so the V-cycle is a
-// symmetric preconditioner.  Coarsest
+// transverse indices, so neighbour lines differ in colour) exactly, in
+// place: lines of up to kPartMaxLine cells are split over up to 8 warps (the
+// partition method, k_line_part), longer ones take one thread each (the
+// Thomas recurrence, k_line).  Pre-smoothing x, y, z (colours 0, 1) and
+// post-smoothing in the exact reverse order, so the V-cycle is a symmetric
+// preconditioner.  Coarsest
 // level (at most 4 cells per axis): exact solve by the separable eigenbases
 // of the coarse operator (A = sum over axes of K_d (x) W_others, K_d E_d =
 // W_d E_d Lambda_d), null mode dropped.

@@ -1,7 +1,8 @@
 """GPU parity: every C-ABI entry point against the FP64 oracle on the same
 seeded inputs (element by element).  Sizes span several 64-wide tiles of the
 pressure-correction transforms with ragged tails, odd and non-cubic shapes,
-the minimum grid, and the 100^3 benchmark grid.
+and the minimum grid; the 100^3 benchmark grid and the 150^3 / 256^3 grids
+are in test_gpu_fullsize.py.
 
 Tolerances (max |gpu - oracle| / max |oracle|):
   FP64 stencils and residual          1e-12  (round-off of ~10^2 terms)

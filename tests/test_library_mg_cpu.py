@@ -87,3 +87,16 @@ def test_bad_arguments(lib):
     assert lib.fv_host_mg_axis(0, 1, 0, ctypes.byref(nout), None, None, None) != 0
     assert lib.fv_host_mg_axis(8, 7, 0, ctypes.byref(nout), None, None, None) != 0
     assert lib.fv_host_mg_levels(0, 4, 4) == -1
+
+
+def test_bench_hierarchy_matches_library(lib):
+    """bench.py counts the multigrid's algorithmic bytes over the same
+    hierarchy the library builds."""
+    import bench
+    for n in (4, 5, 13, 64, 100, 150, 256):
+        lv = bench.mg_levels(n)
+        assert len(lv) == lib.fv_host_mg_levels(n, n, n)
+        for level, cells in enumerate(lv):
+            nout = ctypes.c_int()
+            assert lib.fv_host_mg_axis(n, 1, level, ctypes.byref(nout), None, None, None) == 0
+            assert cells == nout.value ** 3

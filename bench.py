@@ -33,7 +33,7 @@ ALPHA = 0.0
 EPS = 1e-8
 NRHS = 16
 METRIC = "SIMPLE Krylov-vector solves/s (100^3, tol 1e-8)"
-WORKLOAD = "config 2 workload: 100^3 cosine grid, alpha=0, Re=1900, Krylov-vector solve to 1e-8"
+WORKLOAD = "100^3 cosine grid, lid parallel to the x sidewall (alpha=0), Re=1900: SIMPLE Krylov-vector solve to 1e-8"
 
 
 def parse():
